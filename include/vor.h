@@ -1,0 +1,187 @@
+/*
+ * vor.h -- C ABI of the GB300 projector-algorithm library (libvor.so).
+ *
+ * The library computes, on one GPU, the Voronoi diagram of n distinct integer
+ * point sites inside a rectangle X = [0,w] x [0,h] and the Delaunay graph
+ * restricted to X.  It follows D. Reem, "The projector algorithm: a simple
+ * parallel algorithm for computing Voronoi diagrams and Delaunay graphs":
+ *
+ *   - Definition 2.1 defines the cell R_k of site p_k;
+ *   - Theorem 2.2 / eq. (2.1) define the ray endpoint T(p, theta) that every
+ *     ray of the method computes;
+ *   - Algorithm 1 (Section 4) is the per-cell projector run by the kernels;
+ *   - Section 5 defines what is stored per cell (vertices and the lines they
+ *     lie on, labelled by neighbour site), Section 6 the Delaunay graph;
+ *   - Theorem 8.1(c,d) states that cells are independent, which is how the
+ *     work is spread over the GPU.
+ *
+ * Conventions (all entry points):
+ *   - Sites are int32 pairs with 0 < x < w and 0 < y < h (the paper assumes
+ *     sites in the interior of X, Section 2), pairwise distinct, and
+ *     2 <= w, h <= 2^20 (the bound keeps every exact predicate within
+ *     128-bit integers).
+ *   - A line of a cell is labelled by the index j >= 0 of the neighbour site
+ *     whose bisector carries the edge, or by a side of X:
+ *       VOR_SIDE_BOTTOM (-1), VOR_SIDE_RIGHT (-2), VOR_SIDE_TOP (-3),
+ *       VOR_SIDE_LEFT (-4).
+ *   - Cell k lists the lines carrying an edge of positive length, ordered
+ *     counter-clockwise by the polar angle of the edge's outward normal and
+ *     starting at the smallest angle in [0, 2 pi).  Vertex i of cell k is the
+ *     point shared by edges i and i+1 (cyclically), in float64.
+ *   - Delaunay edges are pairs (k, j) with k < j whose cells share an edge of
+ *     positive length, ordered by k, then j.
+ *   - Every pointer named d_* is device memory of the current CUDA device;
+ *     h_* is host memory.  Buffers stay owned by the caller.  All device
+ *     work is ordered on the given stream; nothing is launched on another
+ *     stream.
+ *   - Functions return VOR_OK (0) or a negative VOR_E_* code.  No exception,
+ *     abort or device trap crosses this interface.  After an error the output
+ *     buffers hold unspecified values.
+ */
+#ifndef VOR_H
+#define VOR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VOR_OK 0
+#define VOR_E_INVALID_ARG (-1)   /* null pointer, n < 1, bad option          */
+#define VOR_E_SITE_OUTSIDE (-2)  /* a site on or outside the boundary of X   */
+#define VOR_E_DUPLICATE (-3)     /* two equal sites                          */
+#define VOR_E_BOX_TOO_LARGE (-4) /* w or h outside [2, 2^20]                 */
+#define VOR_E_OOM (-5)           /* workspace or output too small / no memory */
+#define VOR_E_CAPACITY (-6)      /* a cell exceeded the large-cell capacities */
+#define VOR_E_CUDA (-7)          /* a CUDA runtime call failed               */
+#define VOR_E_INTERNAL (-8)      /* an internal consistency check failed     */
+
+#define VOR_SIDE_BOTTOM (-1)
+#define VOR_SIDE_RIGHT (-2)
+#define VOR_SIDE_TOP (-3)
+#define VOR_SIDE_LEFT (-4)
+
+typedef struct vor_site { int32_t x, y; } vor_site;
+typedef struct vor_box { int32_t w, h; } vor_box;
+
+/* Tuning knobs; vor_opts_default() fills the automatic values. */
+typedef struct vor_opts {
+    int32_t bucket_side;      /* bucket side s in units of X (Method A.5); 0: automatic     */
+    int32_t lanes_per_cell;   /* lanes cooperating on one cell: 1,2,4,8,16,32; 0: automatic */
+    int32_t target;           /* sites wanted in the first candidate disc around a site
+                                 (its radius follows the local bucket density); 0: automatic */
+    int32_t exact_only;       /* 1: skip the float filter, decide every ray exactly      */
+    int32_t check_duplicates; /* 1: reject equal sites (VOR_E_DUPLICATE)                  */
+    int32_t collect_stats;    /* 1: fill vor_stats (device atomics, slightly slower)      */
+} vor_opts;
+
+/* Counters of one build (filled when collect_stats = 1). */
+typedef struct vor_stats {
+    uint64_t rays;             /* endpoint computations (rays shot, Algorithm 1)          */
+    uint64_t vertex_tests;     /* "u inside the cell" tests (Algorithm 1)                 */
+    uint64_t evals;            /* candidate evaluations of the float filter                */
+    uint64_t exact_rays;       /* rays or tests the float filter could not decide         */
+    uint64_t annulus_sites;    /* sites checked by the security-radius certificate        */
+    uint64_t reruns;           /* cells recomputed after the certificate added sites      */
+    uint64_t deferred;         /* cells handed to the large-cell kernel                   */
+    uint64_t candidates;       /* candidate sites staged, summed over cells                */
+    uint64_t max_edges;        /* largest e_k                                              */
+    uint64_t widenings;        /* certificate steps that grew the tested region            */
+    uint64_t reserved[6];
+} vor_stats;
+
+/* Device output buffers, allocated by the caller with the capacities below:
+ *   cell_ptr  int64[n + 1]             CSR offsets of cells into the edge arrays
+ *   edge_label int32[edge_cap]         line labels, canonical order per cell
+ *   vx, vy    double[edge_cap]         vertex coordinates
+ *   del_edge  int32[2 * del_cap]       Delaunay pairs (k, j)
+ *   totals    int64[2]                 written: total edges, total Delaunay edges
+ * edge_cap >= vor_edge_capacity(n) and del_cap >= vor_delaunay_capacity(n)
+ * always suffice (the paper bounds sum_k e_k by (|X_e| + 6) n = 10 n for a
+ * rectangle, Lemma NodesO(n), and the Delaunay graph by 3n - 6 edges). */
+typedef struct vor_out {
+    int64_t *cell_ptr;
+    int32_t *edge_label;
+    double *vx, *vy;
+    int32_t *del_edge;
+    int64_t *totals;
+    int64_t edge_cap, del_cap;
+} vor_out;
+
+/* Fill opts with the defaults (automatic bucket size, lanes and disc size,
+ * filter on, duplicate check on, statistics off). */
+void vor_opts_default(vor_opts *opts);
+
+/* Capacities that always suffice for n sites (see vor_out). */
+int64_t vor_edge_capacity(int64_t n);
+int64_t vor_delaunay_capacity(int64_t n);
+
+/* Bytes of device workspace vor_build_async needs for n sites in box with
+ * these options (opts may be NULL for the defaults).  Returns -1 on invalid
+ * arguments. */
+int64_t vor_workspace_bytes(int64_t n, vor_box box, const vor_opts *opts);
+
+/* Build the diagram of n sites d_sites[0..n) (device, int32 pairs) in X.
+ *
+ * d_workspace: ws_bytes >= vor_workspace_bytes(n, box, opts) bytes of device
+ * memory, 256-byte aligned, owned by the caller and not used by anything else
+ * until the stream reaches the end of this call's work.
+ * out: caller-allocated device buffers (see vor_out).
+ * stream: a cudaStream_t (NULL for the legacy default stream).
+ *
+ * Asynchronous: launches the kernels on the stream and returns without
+ * waiting, so validation errors found on the device (VOR_E_SITE_OUTSIDE,
+ * VOR_E_DUPLICATE, VOR_E_CAPACITY) are reported by vor_status() after the
+ * stream has been synchronised.  Argument errors are returned at once.
+ * No memory is allocated; nothing waits on the host. */
+int vor_build_async(const vor_site *d_sites, int64_t n, vor_box box, const vor_opts *opts,
+                    void *d_workspace, int64_t ws_bytes, const vor_out *out, void *stream);
+
+/* Status of the last vor_build_async that used this workspace: VOR_OK or a
+ * device-detected error.  Synchronises the stream, then reads 4 bytes from
+ * the workspace.  stats (may be NULL) receives the counters. */
+int vor_status(const void *d_workspace, void *stream, vor_stats *stats);
+
+/* Synchronous convenience form: allocates workspace and worst-case output
+ * with cudaMallocAsync on the stream, builds, waits, and returns the outputs
+ * (owned by the caller, free with vor_free_result).  *n_edges and *n_del
+ * receive the totals.  The pointers in *out are device pointers. */
+int vor_build(const vor_site *d_sites, int64_t n, vor_box box, const vor_opts *opts,
+              void *stream, vor_out *out, int64_t *n_edges, int64_t *n_del, vor_stats *stats);
+int vor_free_result(vor_out *out, void *stream);
+
+/* End-to-end form with host buffers: copies h_sites to the device, builds,
+ * and copies the results back into caller-allocated host arrays
+ * (h_cell_ptr[n+1], h_edge_label/h_vx/h_vy[edge_cap], h_del_edge[2*del_cap]).
+ * d_workspace/ws_bytes as for vor_build_async; d_scratch must hold
+ * vor_host_scratch_bytes(n) bytes of device memory for the staged copies.
+ * Returns after the results are on the host. */
+int64_t vor_host_scratch_bytes(int64_t n);
+int vor_build_host(const vor_site *h_sites, int64_t n, vor_box box, const vor_opts *opts,
+                   void *d_workspace, int64_t ws_bytes, void *d_scratch, int64_t scratch_bytes,
+                   int64_t *h_cell_ptr, int32_t *h_edge_label, double *h_vx, double *h_vy,
+                   int32_t *h_del_edge, int64_t edge_cap, int64_t del_cap,
+                   int64_t *n_edges, int64_t *n_del, void *stream);
+
+/* Stage timing, off by default.  When enabled, vor_build_async records a
+ * CUDA event on its stream before and after each stage; vor_stage_ms then
+ * waits for the last event and writes the device milliseconds of the last
+ * timed build: ms[0] bucketing (validation, count, scan, scatter, duplicate
+ * check), ms[1] the projector kernel, ms[2] the large-cell pass, ms[3]
+ * compaction (two scans and the CSR/Delaunay kernel).  Returns the number
+ * of values written (<= max_stages) or a negative VOR_E_* code.  One process
+ * wide set of events on the current device: meant for benchmarking one build
+ * at a time. */
+int vor_stage_timing(int enable);
+int vor_stage_ms(float *ms, int max_stages);
+
+/* Human-readable text of a VOR_* code. */
+const char *vor_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VOR_H */

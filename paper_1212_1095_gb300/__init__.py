@@ -1,0 +1,290 @@
+"""GB300 projector-algorithm library: Python binding of libvor.so.
+
+A thin ctypes binding of the C ABI declared in ``include/vor.h``.  PyTorch
+provides the device memory and the stream; every step of the computation runs
+in the library's CUDA kernels.  There is no CPU fallback: if the library is
+missing or no GPU is present, the calls raise.
+
+Names follow the C ABI (``vor_build_async``, ``vor_status``, ...); ``build``
+and ``build_host`` are the convenience forms the tests and the benchmark use.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+from ._build import SO as _SO_PATH
+from ._build import build_library
+
+__all__ = ["VorOpts", "VorStats", "VorOut", "VorError", "build_library", "library",
+           "vor_opts_default", "vor_workspace_bytes", "vor_build_async", "vor_status",
+           "vor_edge_capacity", "vor_delaunay_capacity", "vor_host_scratch_bytes",
+           "vor_build_host", "vor_strerror", "vor_stage_timing", "vor_stage_ms", "build", "build_host", "Diagram",
+           "SIDE_BOTTOM", "SIDE_RIGHT", "SIDE_TOP", "SIDE_LEFT"]
+
+SIDE_BOTTOM, SIDE_RIGHT, SIDE_TOP, SIDE_LEFT = -1, -2, -3, -4
+
+ERROR_NAMES = {0: "VOR_OK", -1: "VOR_E_INVALID_ARG", -2: "VOR_E_SITE_OUTSIDE",
+               -3: "VOR_E_DUPLICATE", -4: "VOR_E_BOX_TOO_LARGE", -5: "VOR_E_OOM",
+               -6: "VOR_E_CAPACITY", -7: "VOR_E_CUDA", -8: "VOR_E_INTERNAL"}
+
+
+class VorError(RuntimeError):
+    def __init__(self, code: int, where: str = ""):
+        self.code = code
+        super().__init__(f"{where}: {ERROR_NAMES.get(code, code)} ({vor_strerror(code)})")
+
+
+class VorSite(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_int32), ("y", ctypes.c_int32)]
+
+
+class VorBox(ctypes.Structure):
+    _fields_ = [("w", ctypes.c_int32), ("h", ctypes.c_int32)]
+
+
+class VorOpts(ctypes.Structure):
+    _fields_ = [("bucket_side", ctypes.c_int32), ("lanes_per_cell", ctypes.c_int32),
+                ("target", ctypes.c_int32), ("exact_only", ctypes.c_int32),
+                ("check_duplicates", ctypes.c_int32), ("collect_stats", ctypes.c_int32)]
+
+
+class VorStats(ctypes.Structure):
+    _fields_ = [("rays", ctypes.c_uint64), ("vertex_tests", ctypes.c_uint64),
+                ("evals", ctypes.c_uint64), ("exact_rays", ctypes.c_uint64),
+                ("annulus_sites", ctypes.c_uint64), ("reruns", ctypes.c_uint64),
+                ("deferred", ctypes.c_uint64), ("candidates", ctypes.c_uint64),
+                ("max_edges", ctypes.c_uint64), ("widenings", ctypes.c_uint64),
+                ("reserved", ctypes.c_uint64 * 6)]
+
+    def as_dict(self) -> dict:
+        return {f: int(getattr(self, f)) for f, _ in self._fields_ if f != "reserved"}
+
+
+class VorOut(ctypes.Structure):
+    _fields_ = [("cell_ptr", ctypes.c_void_p), ("edge_label", ctypes.c_void_p),
+                ("vx", ctypes.c_void_p), ("vy", ctypes.c_void_p),
+                ("del_edge", ctypes.c_void_p), ("totals", ctypes.c_void_p),
+                ("edge_cap", ctypes.c_int64), ("del_cap", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def library():
+    """Load libvor.so (building it first if the sources changed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _SO_PATH if os.path.exists(_SO_PATH) else build_library()
+    lib = ctypes.CDLL(path)
+    P, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    lib.vor_opts_default.argtypes = [P]
+    lib.vor_opts_default.restype = None
+    lib.vor_edge_capacity.argtypes = [i64]
+    lib.vor_edge_capacity.restype = i64
+    lib.vor_delaunay_capacity.argtypes = [i64]
+    lib.vor_delaunay_capacity.restype = i64
+    lib.vor_workspace_bytes.argtypes = [i64, VorBox, P]
+    lib.vor_workspace_bytes.restype = i64
+    lib.vor_build_async.argtypes = [P, i64, VorBox, P, P, i64, P, P]
+    lib.vor_build_async.restype = i32
+    lib.vor_status.argtypes = [P, P, P]
+    lib.vor_status.restype = i32
+    lib.vor_host_scratch_bytes.argtypes = [i64]
+    lib.vor_host_scratch_bytes.restype = i64
+    lib.vor_build_host.argtypes = [P, i64, VorBox, P, P, i64, P, i64, P, P, P, P, P, i64, i64,
+                                   P, P, P]
+    lib.vor_build_host.restype = i32
+    lib.vor_stage_timing.argtypes = [i32]
+    lib.vor_stage_timing.restype = i32
+    lib.vor_stage_ms.argtypes = [P, i32]
+    lib.vor_stage_ms.restype = i32
+    lib.vor_strerror.argtypes = [i32]
+    lib.vor_strerror.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+# ---------------------------------------------------------------- raw ABI ----
+
+def vor_opts_default(**kw) -> VorOpts:
+    o = VorOpts()
+    library().vor_opts_default(ctypes.byref(o))
+    for k, v in kw.items():
+        if v is None:
+            continue
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(o, k, int(v))
+    return o
+
+
+def _box(box) -> VorBox:
+    if isinstance(box, VorBox):
+        return box
+    w, h = (box, box) if isinstance(box, int) else box
+    return VorBox(int(w), int(h))
+
+
+def vor_edge_capacity(n: int) -> int:
+    return int(library().vor_edge_capacity(int(n)))
+
+
+def vor_delaunay_capacity(n: int) -> int:
+    return int(library().vor_delaunay_capacity(int(n)))
+
+
+def vor_workspace_bytes(n: int, box, opts: VorOpts | None = None) -> int:
+    return int(library().vor_workspace_bytes(int(n), _box(box),
+                                             ctypes.byref(opts) if opts is not None else None))
+
+
+def vor_build_async(d_sites_ptr: int, n: int, box, opts: VorOpts, ws_ptr: int, ws_bytes: int,
+                    out: VorOut, stream: int) -> int:
+    return int(library().vor_build_async(ctypes.c_void_p(d_sites_ptr), int(n), _box(box),
+                                         ctypes.byref(opts), ctypes.c_void_p(ws_ptr),
+                                         int(ws_bytes), ctypes.byref(out),
+                                         ctypes.c_void_p(stream)))
+
+
+def vor_status(ws_ptr: int, stream: int) -> tuple[int, VorStats]:
+    st = VorStats()
+    rc = library().vor_status(ctypes.c_void_p(ws_ptr), ctypes.c_void_p(stream), ctypes.byref(st))
+    return int(rc), st
+
+
+def vor_host_scratch_bytes(n: int) -> int:
+    return int(library().vor_host_scratch_bytes(int(n)))
+
+
+def vor_strerror(code: int) -> str:
+    try:
+        return library().vor_strerror(int(code)).decode()
+    except OSError:
+        return "library not loaded"
+
+
+def vor_stage_timing(enable: bool) -> int:
+    return int(library().vor_stage_timing(1 if enable else 0))
+
+
+def vor_stage_ms() -> list[float]:
+    """Device ms of [bucketing, projector, large cells, compaction] of the last build."""
+    buf = (ctypes.c_float * 4)()
+    k = int(library().vor_stage_ms(buf, 4))
+    if k < 0:
+        raise VorError(k, "vor_stage_ms")
+    return [float(buf[i]) for i in range(k)]
+
+
+def vor_build_host(*args) -> int:
+    return int(library().vor_build_host(*args))
+
+
+# ------------------------------------------------------------ convenience ----
+
+@dataclass
+class Diagram:
+    """Result of one build (device tensors unless built with build_host)."""
+    cell_ptr: object      # int64 [n+1]
+    labels: object        # int32 [E]
+    vx: object            # float64 [E]
+    vy: object            # float64 [E]
+    delaunay: object      # int32 [M, 2]
+    stats: dict
+
+
+class Workspace:
+    """Device buffers for repeated builds of up to n sites (torch allocations)."""
+
+    def __init__(self, n: int, box, opts: VorOpts, device=None):
+        import torch
+        self.n, self.box, self.opts = int(n), _box(box), opts
+        dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
+        nb = vor_workspace_bytes(n, self.box, opts)
+        if nb < 0:
+            raise VorError(-1, "vor_workspace_bytes")
+        self.ws = torch.empty(nb + 256, dtype=torch.uint8, device=dev)
+        self.ws_ptr = (self.ws.data_ptr() + 255) & ~255
+        self.ws_bytes = nb
+        ec, dc = vor_edge_capacity(n), vor_delaunay_capacity(n)
+        self.cell_ptr = torch.empty(n + 1, dtype=torch.int64, device=dev)
+        self.labels = torch.empty(ec, dtype=torch.int32, device=dev)
+        self.vx = torch.empty(ec, dtype=torch.float64, device=dev)
+        self.vy = torch.empty(ec, dtype=torch.float64, device=dev)
+        self.del_edge = torch.empty((dc, 2), dtype=torch.int32, device=dev)
+        self.totals = torch.zeros(2, dtype=torch.int64, device=dev)
+        self.out = VorOut(self.cell_ptr.data_ptr(), self.labels.data_ptr(), self.vx.data_ptr(),
+                          self.vy.data_ptr(), self.del_edge.data_ptr(), self.totals.data_ptr(),
+                          ec, dc)
+
+    def launch(self, d_sites, stream=None) -> None:
+        """Enqueue a build of the sites tensor (int32 [n,2], on the device)."""
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream()
+        rc = vor_build_async(d_sites.data_ptr(), d_sites.shape[0], self.box, self.opts,
+                             self.ws_ptr, self.ws_bytes, self.out, s.cuda_stream)
+        if rc != 0:
+            raise VorError(rc, "vor_build_async")
+
+    def finish(self, stream=None) -> Diagram:
+        """Wait for the build, check its status and return views of the output."""
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream()
+        rc, st = vor_status(self.ws_ptr, s.cuda_stream)
+        if rc != 0:
+            raise VorError(rc, "vor_status")
+        ne, nd = (int(v) for v in self.totals.cpu())
+        return Diagram(self.cell_ptr, self.labels[:ne], self.vx[:ne], self.vy[:ne],
+                       self.del_edge[:nd], st.as_dict())
+
+
+def build(sites, box, **opts) -> Diagram:
+    """Voronoi cells and Delaunay edges of ``sites`` (torch int32 [n,2] on the GPU).
+
+    Keyword options are the fields of ``vor_opts`` (bucket_side,
+    lanes_per_cell, target, exact_only, check_duplicates, collect_stats).
+    """
+    import torch
+    if not (hasattr(sites, "is_cuda") and sites.is_cuda):
+        raise TypeError("sites must be a CUDA tensor (int32 [n,2])")
+    sites = sites.to(torch.int32).contiguous()
+    ws = Workspace(sites.shape[0], box, vor_opts_default(**opts), device=sites.device)
+    ws.launch(sites)
+    return ws.finish()
+
+
+def build_host(sites_np, box, **opts):
+    """End-to-end form over host arrays (vor_build_host): returns numpy arrays."""
+    import numpy as np
+    import torch
+    sites_np = np.ascontiguousarray(sites_np, dtype=np.int32)
+    n = sites_np.shape[0]
+    o = vor_opts_default(**opts)
+    b = _box(box)
+    nb = vor_workspace_bytes(n, b, o)
+    if nb < 0:
+        raise VorError(-1, "vor_workspace_bytes")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    ws = torch.empty(nb + 256, dtype=torch.uint8, device=dev)
+    sb = vor_host_scratch_bytes(n)
+    scratch = torch.empty(sb + 256, dtype=torch.uint8, device=dev)
+    ec, dc = vor_edge_capacity(n), vor_delaunay_capacity(n)
+    cell_ptr = np.empty(n + 1, dtype=np.int64)
+    labels = np.empty(ec, dtype=np.int32)
+    vx = np.empty(ec, dtype=np.float64)
+    vy = np.empty(ec, dtype=np.float64)
+    dl = np.empty((dc, 2), dtype=np.int32)
+    ne, nd = ctypes.c_int64(), ctypes.c_int64()
+    P = ctypes.c_void_p
+    rc = vor_build_host(P(sites_np.ctypes.data), n, b, ctypes.byref(o),
+                        P((ws.data_ptr() + 255) & ~255), nb, P((scratch.data_ptr() + 255) & ~255),
+                        sb, P(cell_ptr.ctypes.data), P(labels.ctypes.data), P(vx.ctypes.data),
+                        P(vy.ctypes.data), P(dl.ctypes.data), ec, dc, ctypes.byref(ne),
+                        ctypes.byref(nd), P(torch.cuda.current_stream().cuda_stream))
+    if rc != 0:
+        raise VorError(rc, "vor_build_host")
+    return Diagram(cell_ptr, labels[:ne.value], vx[:ne.value], vy[:ne.value], dl[:nd.value], {})

@@ -1,0 +1,35 @@
+// vor_cells.cu -- launchers of the projector kernel: lane-count dispatch of
+// the first pass and the large-cell pass (one warp per deferred cell).
+#include "vor_cells.cuh"
+
+namespace vor {
+
+int cells_fast_max_smem() { return (int)(F_GROUPS * sizeof(FastSmem)); }
+int cells_large_capacity() { return L_CMAX; }
+
+cudaError_t launch_cells_fast(const CellParams &P, int lanes, cudaStream_t st) {
+    switch (lanes) {
+    case 2: return launch_fast_g<2>(P, st);
+    case 4: return launch_fast_g<4>(P, st);
+    case 8: return launch_fast_g<8>(P, st);
+    case 16: return launch_fast_g<16>(P, st);
+    case 32: return launch_fast_g<32>(P, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_cells_large(const CellParams &P, int max_cells, cudaStream_t st) {
+    auto kern = cells_kernel<32, L_CMAX, L_SMAX, L_EMAX, L_RMAX, true>;
+    const int smem = (int)sizeof(LargeSmem);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int grid = sms * 2;
+    if (max_cells < grid) grid = max_cells > 0 ? max_cells : 1;
+    kern<<<grid, 32, smem, st>>>(P);
+    return cudaGetLastError();
+}
+
+}  // namespace vor

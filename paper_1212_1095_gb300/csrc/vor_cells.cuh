@@ -1,0 +1,647 @@
+// vor_cells.cuh -- the per-cell projector kernel (ray shooting).
+//
+// A group of G lanes of one warp computes one Voronoi cell with Algorithm 1
+// of the paper; a warp holds 32/G groups, each on its own cell.
+//
+//  1. Candidates.  The sites within distance rho of p (found through the
+//     buckets of Method A.5 that meet the square [p - rho, p + rho]) are
+//     staged in shared memory, with the four sides of X written as lines (the
+//     reflection of p across a side has that side as its bisector with p, so
+//     eq. (A.1) is a bisector hit like any other).
+//  2. Projector.  The three projector corners are shot, then the subedges are
+//     processed depth-first, left child first, so subwedges are visited
+//     counter-clockwise and the cell's edges come out in that order.  The
+//     loop is a state machine that issues exactly one ray per iteration from
+//     a single call site, so the groups of a warp stay converged while they
+//     scan their candidates.  A ray's endpoint T(p, theta) (eq. (2.1)) is the
+//     candidate line with the largest key K = <n, theta> / c: lanes split the
+//     candidates, evaluate an FP32 filter with a certified error bound and
+//     reduce with warp shuffles; only rays whose winner the bound cannot
+//     separate (near ties, and exact ties where the ray meets a vertex,
+//     Remark A.4) are re-decided exactly in 128-bit integers, again split
+//     over the lanes.  The test "u is inside the cell" of Algorithm 1 is the
+//     ray towards u: u is inside iff no line other than L1, L2 is met first.
+//  3. Certificate.  R = the largest distance from p to a vertex of the
+//     polygon.  A site farther than 2R cannot cut it (for x in the polygon,
+//     |x - a| >= |a - p| - |x - p| > R >= |x - p|; the argument of Lemmas
+//     Byy'Syy' and SitesInLargeSquare).  All sites within rho were
+//     candidates; while 2R > rho, rho grows (at most doubling), the new sites
+//     are tested against the polygon's vertices, the ones that cut it join
+//     the candidates and the projector runs again.
+//  4. Output.  The edge labels are rotated to start at the smallest normal
+//     angle and written to a fixed slot per cell (or a spill area).
+//
+// The first pass (small capacities, bounded certificate work) defers the
+// rare cells that exceed its limits; the same code with large capacities and
+// one warp per cell completes them.
+#pragma once
+
+#include <cfloat>
+#include <cmath>
+
+#include "vor_device.cuh"
+#include "vor_internal.h"
+
+namespace vor {
+
+template <int CMAX, int SMAX, int EMAX>
+struct __align__(16) GroupSmem {
+    float4 cand[CMAX];           // nx, ny, 1/c, (|nx|+|ny|)/c
+    int lab[CMAX];               // site index (>= 0) or side (-1..-4)
+    long long sx[SMAX], sy[SMAX];// subedge stack: right corners
+    short scw[SMAX], sccw[SMAX]; // their clockwise / counter-clockwise lines
+    short emit[EMAX];            // edges, counter-clockwise
+    float vx[EMAX], vy[EMAX];    // approximate vertices relative to p
+    int ncand;                   // candidate count while appending
+    int flag;
+};
+
+struct Hit { int ccw, cw; };
+
+struct Counters {
+    unsigned long long rays, vtests, evals, exact, annulus, reruns, deferred, cands, maxe, widen;
+};
+
+enum { CELL_OK = 0, CELL_DEFER = 1, CELL_FAIL = 2 };
+
+// Float filter: the computed key k of a candidate satisfies
+//   |k - K| <= 6.1 u (|nx||tx| + |ny||ty|) / c,  u = 2^-24
+// (rounding of theta to float, of the dot product and of 1/c).  The kernel
+// uses tol = (|nx|+|ny|)/c * max(|tx|,|ty|) * 2^-19 (= 32 u), a margin of
+// more than 5x, which also absorbs the rounding of k + tol and k - tol.
+#define VOR_TOL_SCALE 0x1p-19f
+
+struct Filt { float u1, ls, u2, ux; int i1; };
+
+template <int G>
+__device__ __forceinline__ void filt_reduce(Filt &f, unsigned gmask) {
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) {
+        float ou1 = __shfl_xor_sync(gmask, f.u1, off, G);
+        float ols = __shfl_xor_sync(gmask, f.ls, off, G);
+        float ou2 = __shfl_xor_sync(gmask, f.u2, off, G);
+        float oux = __shfl_xor_sync(gmask, f.ux, off, G);
+        int oi1 = __shfl_xor_sync(gmask, f.i1, off, G);
+        bool take = (ou1 > f.u1) || (ou1 == f.u1 && oi1 < f.i1);
+        float lo = take ? f.u1 : ou1;
+        f.u2 = fmaxf(fmaxf(f.u2, ou2), lo);
+        if (take) { f.u1 = ou1; f.i1 = oi1; f.ls = ols; }
+        f.ux = fmaxf(f.ux, oux);
+    }
+}
+
+template <class SM>
+__device__ __forceinline__ void cand_int(const SM &S, int c, int &nx, int &ny, i64 &cc) {
+    float4 q = S.cand[c];
+    nx = __float2int_rn(q.x);
+    ny = __float2int_rn(q.y);
+    cc = line_c(nx, ny, S.lab[c] < 0);
+}
+
+// a strictly more counter-clockwise than b (normals in one open half-plane)
+template <class SM>
+__device__ __forceinline__ bool more_ccw(const SM &S, int a, int b) {
+    int ax, ay, bx, by;
+    i64 ca, cb;
+    cand_int(S, a, ax, ay, ca);
+    cand_int(S, b, bx, by, cb);
+    return (i64)bx * ay - (i64)by * ax > 0;
+}
+
+// merge (best, ccw, cw) with (ob, occ, ocw) for direction (tx, ty), exactly
+template <class SM>
+__device__ __forceinline__ void exact_merge(const SM &S, i64 tx, i64 ty, int &best, int &ccw,
+                                            int &cw, int ob, int occ, int ocw) {
+    if (ob < 0) return;
+    if (best < 0) { best = ob; ccw = occ; cw = ocw; return; }
+    int ax, ay, bx, by;
+    i64 ca, cb;
+    cand_int(S, best, ax, ay, ca);
+    cand_int(S, ob, bx, by, cb);
+    i128 da = dot128(ax, ay, tx, ty), db = dot128(bx, by, tx, ty);
+    i128 lhs = db * (i128)ca, rhs = da * (i128)cb;   // key(ob) vs key(best)
+    if (lhs > rhs) { best = ob; ccw = occ; cw = ocw; }
+    else if (lhs == rhs) {
+        if (more_ccw(S, occ, ccw)) ccw = occ;
+        if (more_ccw(S, cw, ocw)) cw = ocw;
+    }
+}
+
+// Exact endpoint of direction (tx, ty) over the candidates whose filter upper
+// bound reaches thr (all candidates when use_thr is false).
+template <int G, class SM>
+__device__ Hit exact_argmax(const SM &S, int C, i64 tx, i64 ty, float fx, float fy, float eth,
+                            bool use_thr, float thr, int gl, unsigned gmask) {
+    int best = -1, ccw = -1, cw = -1;
+    for (int c = gl; c < C; c += G) {
+        float4 q = S.cand[c];
+        if (use_thr) {
+            float den = fmaf(q.x, fx, q.y * fy);
+            float U = fmaf(den, q.z, q.w * eth);
+            if (!(U >= thr)) continue;
+        }
+        int nx = __float2int_rn(q.x), ny = __float2int_rn(q.y);
+        if (dot128(nx, ny, tx, ty) <= 0) continue;
+        exact_merge(S, tx, ty, best, ccw, cw, c, c, c);
+    }
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) {
+        int ob = __shfl_xor_sync(gmask, best, off, G);
+        int oc = __shfl_xor_sync(gmask, ccw, off, G);
+        int ow = __shfl_xor_sync(gmask, cw, off, G);
+        exact_merge(S, tx, ty, best, ccw, cw, ob, oc, ow);
+    }
+    return Hit{ccw, cw};
+}
+
+// Sign of cross(a, b) = ax by - ay bx for 64-bit integer vectors: a float
+// evaluation with a bound on its error, the exact 128-bit value when the
+// bound cannot decide.
+__device__ __forceinline__ int cross_sign(i64 ax, i64 ay, i64 bx, i64 by) {
+    const float p = (float)ax * (float)by, q = (float)ay * (float)bx;
+    const float v = p - q, bound = (fabsf(p) + fabsf(q)) * 0x1p-20f;
+    if (v > bound) return 1;
+    if (v < -bound) return -1;
+    const i128 e = cross128(ax, ay, bx, by);
+    return e > 0 ? 1 : (e < 0 ? -1 : 0);
+}
+
+enum { Q_SHOOT = 0, Q_UTEST = 1 };
+
+// Algorithm 1 over the C staged candidates.  Returns the number of edges (in
+// S.emit, counter-clockwise from the edge met by psi_1), or -1 when a
+// capacity is exceeded.
+template <int G, int CMAX, int SMAX, int EMAX, int RMAX>
+__device__ int projector(GroupSmem<CMAX, SMAX, EMAX> &S, const int C, const int gl,
+                         const unsigned gmask, const int exact_only, Counters &cnt) {
+    int phase = 0;                  // 0..2: the projector corners; 3: the subedges
+    Hit init[3];
+    i64 lx = 0, ly = 0;             // left corner of the current subwedge
+    int llab = -1;                  // its line (the counter-clockwise extreme)
+    int sp = 0, ne = 0, rays = 3, first = -1, last = -1;
+    for (int guard = 0; guard < 4 * RMAX + 8; guard++) {
+        // ---- choose the next ray (control only, no candidate scans) ----
+        int qt = Q_SHOOT;
+        i64 tx = 0, ty = 0, Nx = 0, Ny = 0, D = 0;
+        int la = -1, lb = -1;
+        if (phase < 3) {
+            tx = phase == 0 ? 2 : (phase == 1 ? 0 : -2);
+            ty = phase == 1 ? 1 : -1;
+        } else {
+            bool have = false;
+            while (sp > 0) {
+                const int top = sp - 1;
+                const i64 rx = S.sx[top], ry = S.sy[top];
+                const int rcw = S.scw[top];
+                if (llab == rcw) {                         // same line: no vertex here
+                    if (llab != last) {
+                        if (ne >= EMAX) return -1;
+                        if (gl == 0) S.emit[ne] = (short)llab;
+                        if (first < 0) first = llab;
+                        last = llab;
+                        ne++;
+                    }
+                    lx = rx; ly = ry; llab = S.sccw[top];
+                    sp--;
+                    continue;
+                }
+                int n1x, n1y, n2x, n2y;
+                i64 c1, c2;
+                cand_int(S, llab, n1x, n1y, c1);
+                cand_int(S, rcw, n2x, n2y, c2);
+                intersect(n1x, n1y, c1, n2x, n2y, c2, Nx, Ny, D);
+                la = llab;
+                lb = rcw;
+                if (D == 0) {                              // parallel lines
+                    tx = -(i64)n1y;
+                    ty = (i64)n1x;
+                    if (!(cross128(lx, ly, tx, ty) >= 0 && cross128(tx, ty, rx, ry) >= 0)) {
+                        tx = -tx;
+                        ty = -ty;
+                    }
+                    la = lb = -1;
+                } else {
+                    const int sg = D > 0 ? 1 : -1;
+                    const bool inw = sg * cross_sign(lx, ly, Nx, Ny) >= 0 &&
+                                     sg * cross_sign(Nx, Ny, rx, ry) >= 0;   // lambda >= 0
+                    tx = sg * Nx;
+                    ty = sg * Ny;
+                    if (inw) {
+                        qt = Q_UTEST;                      // ray towards u
+                    } else {
+                        tx = -tx;                          // theta_3 := p - u
+                        ty = -ty;
+                        la = lb = -1;
+                    }
+                }
+                have = true;
+                break;
+            }
+            if (!have) break;                              // EdgeQueue is empty
+        }
+        // ---- one filter pass over the candidates (the only call site) ----
+        const float fx = (float)tx, fy = (float)ty;
+        const float eth = fmaxf(fabsf(fx), fabsf(fy)) * VOR_TOL_SCALE;
+        Filt f{-FLT_MAX, -FLT_MAX, -FLT_MAX, -FLT_MAX, -1};
+        for (int c = gl; c < C; c += G) {
+            const float4 q = S.cand[c];
+            const float den = fmaf(q.x, fx, q.y * fy);
+            const float tol = q.w * eth;
+            const float U = fmaf(den, q.z, tol);
+            const float L = fmaf(den, q.z, -tol);
+            if (U > f.u1) { f.u2 = f.u1; f.u1 = U; f.i1 = c; f.ls = L; }
+            else f.u2 = fmaxf(f.u2, U);
+            if (c != la && c != lb) f.ux = fmaxf(f.ux, U);
+        }
+        filt_reduce<G>(f, gmask);
+        cnt.evals += C;
+        // ---- decide ----
+        Hit h{-1, -1};
+        bool inside = false;
+        if (qt == Q_UTEST) {
+            cnt.vtests++;
+            const i64 aD = D > 0 ? D : -D;
+            const float kuf = (float)(aD / 2);             // key of u: |D|/2, an integer
+            const float klo = kuf * (1.f - 0x1p-21f), khi = kuf * (1.f + 0x1p-21f);
+            if (!exact_only && f.ux < klo) {
+                inside = true;
+            } else if (!exact_only && f.ls > f.u2 && f.ls > khi && f.i1 != la && f.i1 != lb) {
+                h = Hit{f.i1, f.i1};
+            } else {
+                cnt.exact++;
+                // exact: u violates line c iff 2 <n_c, N> sgn(D) > c |D|
+                int viol = 0;
+                for (int c = gl; c < C && !viol; c += G) {
+                    if (c == la || c == lb) continue;
+                    if (!exact_only) {
+                        const float4 q = S.cand[c];
+                        const float den = fmaf(q.x, fx, q.y * fy);
+                        if (fmaf(den, q.z, q.w * eth) < klo) continue;
+                    }
+                    int nx, ny;
+                    i64 cc;
+                    cand_int(S, c, nx, ny, cc);
+                    const i128 lhs = 2 * dot128(nx, ny, Nx, Ny) * (i128)(D > 0 ? 1 : -1);
+                    if (lhs > (i128)cc * aD) viol = 1;
+                }
+                viol = group_or<G>(viol, gmask);
+                if (!viol) inside = true;
+                else h = exact_argmax<G>(S, C, tx, ty, fx, fy, eth, !exact_only, f.ls, gl, gmask);
+            }
+        } else {
+            cnt.rays++;
+            if (!exact_only && f.ls > f.u2 && f.ls > 0.f) {
+                h = Hit{f.i1, f.i1};
+            } else {
+                cnt.exact++;
+                h = exact_argmax<G>(S, C, tx, ty, fx, fy, eth, !exact_only, f.ls, gl, gmask);
+            }
+        }
+        // ---- update the subedge state ----
+        if (phase < 3) {
+            init[phase] = h;
+            if (h.ccw < 0) return -1;
+            if (++phase == 3) {
+                lx = 2; ly = -1; llab = init[0].ccw;
+                if (gl == 0) {
+                    S.sx[0] = 2;  S.sy[0] = -1; S.scw[0] = (short)init[0].cw; S.sccw[0] = (short)init[0].ccw;
+                    S.sx[1] = -2; S.sy[1] = -1; S.scw[1] = (short)init[2].cw; S.sccw[1] = (short)init[2].ccw;
+                    S.sx[2] = 0;  S.sy[2] = 1;  S.scw[2] = (short)init[1].cw; S.sccw[2] = (short)init[1].ccw;
+                }
+                sp = 3;
+            }
+        } else if (inside) {                               // u is a vertex: L1, L2 are edges
+            const int top = sp - 1;
+            if (la != last) {
+                if (ne >= EMAX) return -1;
+                if (gl == 0) S.emit[ne] = (short)la;
+                if (first < 0) first = la;
+                last = la;
+                ne++;
+            }
+            if (lb != last) {
+                if (ne >= EMAX) return -1;
+                if (gl == 0) S.emit[ne] = (short)lb;
+                if (first < 0) first = lb;
+                last = lb;
+                ne++;
+            }
+            lx = S.sx[top]; ly = S.sy[top]; llab = S.sccw[top];
+            sp--;
+        } else {                                           // divide the subedge at theta_3
+            if (sp >= SMAX || ++rays > RMAX || h.ccw < 0) return -1;
+            if (gl == 0) {
+                S.sx[sp] = tx; S.sy[sp] = ty; S.scw[sp] = (short)h.cw; S.sccw[sp] = (short)h.ccw;
+            }
+            sp++;
+        }
+        group_sync<G>(gmask);
+    }
+    group_sync<G>(gmask);
+    if (phase < 3 || sp > 0) return -1;
+    if (ne > 1 && last == first) ne--;                     // the walk closes on its first edge
+    return ne;
+}
+
+// Append to the candidates the sites a != p with r2lo < |a - p|^2 <= r2hi
+// (all of them, or with cut_only those that cut the polygon S.vx/S.vy of e
+// vertices), scanning the buckets that meet the square of half-side
+// sqrt(r2hi) around p.  Uses S.ncand as the append counter and sets S.flag
+// when the table would grow past cap.  Returns the number of sites examined
+// (for the work budget).
+template <int G, int CMAX, int SMAX, int EMAX>
+__device__ int scan_disc(const CellParams &P, GroupSmem<CMAX, SMAX, EMAX> &S, const int2 p,
+                         const int self, const i64 r2lo, const i64 r2hi, const bool cut_only,
+                         const int e, const int cap, const int gl, Counters &cnt) {
+    const int s = P.s;
+    const int r = (int)ceilf(sqrtf((float)r2hi)) + 1;
+    const int bx0 = p.x - r <= 0 ? 0 : (p.x - r) / s;
+    const int bx1 = min(P.m1 - 1, (p.x + r) / s);
+    const int by0 = p.y - r <= 0 ? 0 : (p.y - r) / s;
+    const int by1 = min(P.m2 - 1, (p.y + r) / s);
+    int seen = 0;
+    for (int row = by0; row <= by1; row++) {
+        const int a = P.bstart[row * P.m1 + bx0], b = P.bstart[row * P.m1 + bx1 + 1];
+        seen += b - a;
+        for (int pos = a + gl; pos < b; pos += G) {
+            if (pos == self) continue;
+            const int2 q = P.sxy[pos];
+            const int nx = q.x - p.x, ny = q.y - p.y;
+            const i64 cc = (i64)nx * nx + (i64)ny * ny;
+            if (cc <= r2lo || cc > r2hi) continue;
+            const float fnx = (float)nx, fny = (float)ny, fc = (float)cc;
+            if (cut_only) {
+                cnt.annulus++;
+                bool cut = false;
+                for (int v = 0; v < e && !cut; v++) {
+                    const float vx = S.vx[v], vy = S.vy[v];
+                    const float f = 2.f * fmaf(fnx, vx, fny * vy) - fc;
+                    const float mg = 0x1p-16f * (2.f * (fabsf(fnx * vx) + fabsf(fny * vy)) + fc);
+                    if (f > mg) cut = true;
+                    else if (f >= -mg) {
+                        const int la = S.emit[v], lb = S.emit[v + 1 < e ? v + 1 : 0];
+                        int n1x, n1y, n2x, n2y;
+                        i64 c1, c2, Nx, Ny, D;
+                        cand_int(S, la, n1x, n1y, c1);
+                        cand_int(S, lb, n2x, n2y, c2);
+                        intersect(n1x, n1y, c1, n2x, n2y, c2, Nx, Ny, D);
+                        const i128 lhs = 2 * dot128(nx, ny, Nx, Ny) * (i128)(D > 0 ? 1 : -1);
+                        const i128 rhs = (i128)cc * (D > 0 ? D : -D);
+                        if (lhs > rhs) cut = true;
+                    }
+                }
+                if (!cut) continue;
+            }
+            const int at = atomicAdd(&S.ncand, 1);
+            if (at < cap) {
+                const float rc = 1.f / fc;
+                S.cand[at] = make_float4(fnx, fny, rc, (float)(abs(nx) + abs(ny)) * rc);
+                S.lab[at] = P.sid[pos];
+            } else {
+                S.flag = 1;
+            }
+        }
+    }
+    return seen;
+}
+
+// vertices of the polygon (S.emit, e edges) into S.vx/S.vy; returns max |v-p|^2
+template <int G, int CMAX, int SMAX, int EMAX>
+__device__ float polygon_vertices(GroupSmem<CMAX, SMAX, EMAX> &S, const int e, const int gl,
+                                  const unsigned gmask) {
+    float R2 = 0.f;
+    for (int q = gl; q < e; q += G) {
+        const int a = S.emit[q], b = S.emit[q + 1 < e ? q + 1 : 0];
+        int n1x, n1y, n2x, n2y;
+        i64 c1, c2, Nx, Ny, D;
+        cand_int(S, a, n1x, n1y, c1);
+        cand_int(S, b, n2x, n2y, c2);
+        intersect(n1x, n1y, c1, n2x, n2y, c2, Nx, Ny, D);
+        if (D == 0) { S.flag = 2; continue; }
+        const float rd = 1.f / (float)D;
+        const float vx = (float)Nx * rd, vy = (float)Ny * rd;
+        S.vx[q] = vx;
+        S.vy[q] = vy;
+        R2 = fmaxf(R2, fmaf(vx, vx, vy * vy));
+    }
+    return group_max<G>(R2, gmask);
+}
+
+// Work limits of a pass: the first pass defers cells that need more.
+template <bool LARGE>
+struct Limits {
+    static constexpr int widen = LARGE ? 64 : 2;          // certificate steps
+    static constexpr int scan = LARGE ? (1 << 30) : 384;  // sites examined
+};
+
+template <int G, int CMAX, int SMAX, int EMAX, int RMAX, bool LARGE>
+__device__ int process_cell(const CellParams &P, GroupSmem<CMAX, SMAX, EMAX> &S, int i, int gl,
+                            unsigned gmask, Counters &cnt) {
+    const int2 p = P.sxy[i];
+    const int k = P.sid[i];
+
+    // ---- 1. candidates: the sites within rho of p, then the four sides --------
+    // rho is chosen so that about P.target sites fall in the disc, from the
+    // site density of the 3x3 buckets around p's bucket
+    const int s = P.s;
+    const int bx = p.x / s, by = p.y / s;
+    int c9 = 0, nb9 = 0;
+    {
+        const int x0 = max(bx - 1, 0), x1 = min(bx + 1, P.m1 - 1);
+        for (int row = max(by - 1, 0); row <= min(by + 1, P.m2 - 1); row++) {
+            c9 += P.bstart[row * P.m1 + x1 + 1] - P.bstart[row * P.m1 + x0];
+            nb9 += x1 - x0 + 1;
+        }
+    }
+    const i64 cxf = max(p.x, P.W - p.x), cyf = max(p.y, P.H - p.y);
+    const i64 far2 = cxf * cxf + cyf * cyf;           // no site is farther than a corner
+    const float area = (float)nb9 * (float)s * (float)s;
+    i64 rho2 = (i64)((float)P.target * area / (3.14159265f * (float)max(c9 - 1, 1)));
+    rho2 = max(min(rho2, (i64)(16.f * (float)s * (float)s)), (i64)4);
+    int scanned = 0;
+    for (int attempt = 0;; attempt++) {
+        if (gl == 0) { S.ncand = 0; S.flag = 0; }
+        group_sync<G>(gmask);
+        scanned += scan_disc<G>(P, S, p, i, -1, rho2, false, 0, CMAX - 4, gl, cnt);
+        group_sync<G>(gmask);
+        if (!S.flag) break;
+        if (!LARGE || attempt >= 24 || rho2 <= 4) return CELL_DEFER;
+        rho2 /= 4;                                     // too dense: a smaller disc
+    }
+    int C = S.ncand;
+    if (gl == 0) {
+        const int sx[4] = {0, P.W - p.x, 0, -p.x};
+        const int sy[4] = {-p.y, 0, P.H - p.y, 0};
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const float cf = (float)(2 * ((i64)sx[q] * sx[q] + (i64)sy[q] * sy[q]));
+            const float rc = 1.f / cf;
+            S.cand[C + q] = make_float4((float)sx[q], (float)sy[q], rc,
+                                        (float)(abs(sx[q]) + abs(sy[q])) * rc);
+            S.lab[C + q] = -1 - q;
+        }
+    }
+    C += 4;
+    cnt.cands += C;
+    group_sync<G>(gmask);
+
+    // ---- 2. Algorithm 1 ----------------------------------------------------
+    int e = projector<G, CMAX, SMAX, EMAX, RMAX>(S, C, gl, gmask, P.exact_only, cnt);
+    if (e < 0) return CELL_DEFER;
+    if (e < 3) return CELL_FAIL;
+
+    // ---- 3. security-radius certificate -------------------------------------
+    // every site a with |a - p|^2 > rho2 has not been looked at and is
+    // farther than rho
+    for (int iter = 0;; iter++) {
+        const float R2 = polygon_vertices<G>(S, e, gl, gmask);
+        group_sync<G>(gmask);
+        if (S.flag == 2) return CELL_FAIL;
+        const i64 need = (i64)(4.f * (R2 * (1.f + 0x1p-12f) + 1.f)) + 1;   // > (2R)^2
+        if (need <= rho2 || rho2 >= far2) break;                          // certified
+        if (iter >= Limits<LARGE>::widen) return LARGE ? CELL_FAIL : CELL_DEFER;
+        cnt.widen++;
+        const i64 grow = rho2 < ((i64)1 << 60) / 4 ? 4 * rho2 + 4 : rho2;
+        const i64 rho2n = min(min(need, grow), far2);
+        if (!LARGE) {
+            const int r = (int)ceilf(sqrtf((float)rho2n)) + 1;
+            const i64 nb = (i64)(2 * r / s + 2) * (2 * r / s + 2);
+            if (nb * 4 > Limits<LARGE>::scan) return CELL_DEFER;
+        }
+        if (gl == 0) S.ncand = C;
+        group_sync<G>(gmask);
+        scanned += scan_disc<G>(P, S, p, i, rho2, rho2n, true, e, CMAX, gl, cnt);
+        rho2 = rho2n;
+        group_sync<G>(gmask);
+        if (S.flag) return CELL_DEFER;
+        const int ncut = S.ncand - C;
+        if (ncut > 0) {
+            cnt.reruns++;
+            C += ncut;
+            cnt.cands += ncut;
+            e = projector<G, CMAX, SMAX, EMAX, RMAX>(S, C, gl, gmask, P.exact_only, cnt);
+            if (e < 0) return CELL_DEFER;
+            if (e < 3) return CELL_FAIL;
+        }
+        if (!LARGE && scanned > Limits<LARGE>::scan) return CELL_DEFER;
+    }
+
+    // ---- 4. canonical order and output ----------------------------------
+    int start = 0;
+    {
+        int bxn, byn;
+        i64 dummy;
+        cand_int(S, S.emit[0], bxn, byn, dummy);
+        for (int q = 1; q < e; q++) {
+            int qx, qy;
+            cand_int(S, S.emit[q], qx, qy, dummy);
+            if (angle_less(qx, qy, bxn, byn)) { start = q; bxn = qx; byn = qy; }
+        }
+    }
+    int *dst;
+    int off = -1;
+    if (e <= SLOT_CAP) {
+        dst = P.slot + (size_t)k * SLOT_CAP;
+    } else {
+        if (gl == 0) off = atomicAdd(&P.hdr->spill_top, e);
+        off = __shfl_sync(gmask, off, 0, G);
+        if (off + e > P.spill_cap) return CELL_DEFER;
+        dst = P.spill + off;
+    }
+    int dcnt = 0;
+    for (int q = gl; q < e; q += G) {
+        int qq = start + q;
+        if (qq >= e) qq -= e;
+        const int lab = S.lab[S.emit[qq]];
+        dst[q] = lab;
+        dcnt += lab > k ? 1 : 0;
+    }
+    dcnt = group_sum<G>(dcnt, gmask);
+    if (gl == 0) {
+        P.ecount[k] = e;
+        P.dcount[k] = dcnt;
+        P.loc[k] = off;
+    }
+    if ((unsigned long long)e > cnt.maxe) cnt.maxe = e;
+    group_sync<G>(gmask);
+    return CELL_OK;
+}
+
+template <int G, int CMAX, int SMAX, int EMAX, int RMAX, bool LARGE>
+__global__ void cells_kernel(CellParams P) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    using SM = GroupSmem<CMAX, SMAX, EMAX>;
+    if (P.hdr->err) return;
+    const int lane = threadIdx.x & 31;
+    const int gib = threadIdx.x / G;
+    const int gl = threadIdx.x % G;
+    const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << ((lane / G) * G));
+    SM &S = reinterpret_cast<SM *>(smem_raw)[gib];
+    const int gpb = blockDim.x / G;
+    const int total = P.cell_list ? *P.list_count : P.n;
+    Counters cnt{};
+    for (int t = blockIdx.x * gpb + gib; t < total; t += gridDim.x * gpb) {
+        const int i = P.cell_list ? P.cell_list[t] : t;
+        const int rc = process_cell<G, CMAX, SMAX, EMAX, RMAX, LARGE>(P, S, i, gl, gmask, cnt);
+        if (rc != CELL_OK && gl == 0) {
+            if (rc == CELL_DEFER && P.deferred) {
+                const int q = atomicAdd(P.deferred_count, 1);
+                P.deferred[q] = i;
+                cnt.deferred++;
+            } else {
+                atomicOr(&P.hdr->err, rc == CELL_DEFER ? ERRB_CAPACITY : ERRB_INTERNAL);
+            }
+        }
+        group_sync<G>(gmask);
+    }
+    if (P.collect_stats && gl == 0) {
+        unsigned long long *st = P.hdr->stats;
+        atomicAdd(&st[STAT_RAYS], cnt.rays);
+        atomicAdd(&st[STAT_VTESTS], cnt.vtests);
+        atomicAdd(&st[STAT_EVALS], cnt.evals);
+        atomicAdd(&st[STAT_EXACT], cnt.exact);
+        atomicAdd(&st[STAT_ANNULUS], cnt.annulus);
+        atomicAdd(&st[STAT_RERUNS], cnt.reruns);
+        atomicAdd(&st[STAT_DEFERRED], cnt.deferred);
+        atomicAdd(&st[STAT_CANDIDATES], cnt.cands);
+        atomicMax(&st[STAT_MAXE], cnt.maxe);
+        atomicAdd(&st[STAT_WIDEN], cnt.widen);
+    }
+}
+
+// ---- configurations ----------------------------------------------------------
+// first pass: 16 groups per block, small capacities, bounded certificate work
+constexpr int F_CMAX = 48, F_SMAX = 20, F_EMAX = 40, F_RMAX = 40, F_GROUPS = 16;
+// large-cell pass: one warp per cell, one cell per block
+constexpr int L_CMAX = 4096, L_SMAX = 512, L_EMAX = 1024, L_RMAX = 2048;
+
+using FastSmem = GroupSmem<F_CMAX, F_SMAX, F_EMAX>;
+using LargeSmem = GroupSmem<L_CMAX, L_SMAX, L_EMAX>;
+
+template <int G>
+cudaError_t launch_fast_g(const CellParams &P, cudaStream_t st) {
+    auto kern = cells_kernel<G, F_CMAX, F_SMAX, F_EMAX, F_RMAX, false>;
+    const int smem = F_GROUPS * (int)sizeof(FastSmem);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, F_GROUPS * G, smem);
+    if (per_sm < 1) per_sm = 1;
+    const int total = P.cell_list ? P.n_list : P.n;
+    long long want = ((long long)total + F_GROUPS - 1) / F_GROUPS;
+    long long grid = (long long)sms * per_sm;
+    if (want < grid) grid = want;
+    if (grid < 1) grid = 1;
+    kern<<<(unsigned)grid, F_GROUPS * G, smem, st>>>(P);
+    return cudaGetLastError();
+}
+
+extern template cudaError_t launch_fast_g<2>(const CellParams &, cudaStream_t);
+extern template cudaError_t launch_fast_g<4>(const CellParams &, cudaStream_t);
+extern template cudaError_t launch_fast_g<8>(const CellParams &, cudaStream_t);
+extern template cudaError_t launch_fast_g<16>(const CellParams &, cudaStream_t);
+extern template cudaError_t launch_fast_g<32>(const CellParams &, cudaStream_t);
+
+}  // namespace vor

@@ -1,0 +1,417 @@
+// vor_cells_persist.cuh -- the first pass of the projector: gather kernel and
+// persistent one-thread-per-cell projector kernel.
+//
+// gather_kernel (one thread per cell): picks the disc radius rho from the
+// site density of the 3x3 buckets around p (about `target` sites inside) and
+// lists the sorted positions of the sites within rho.
+//
+// cells_persist_kernel: every thread works through a sequence of cells; a
+// cell is loaded from its list into the thread's shared-memory candidate
+// table, Algorithm 1 runs one ray per loop iteration, and when the cell's
+// EdgeQueue is empty the thread finalises it (certificate check, canonical
+// output) and takes its next cell.  Loading and finalising are batched with
+// warp ballots: a thread that finished waits until several lanes of its warp
+// are idle, so the per-cell bookkeeping runs with many lanes active and the
+// candidate scans of the rays stay converged across the warp.  A cell whose
+// disc does not certify the polygon (2R > rho) is handed to the second pass,
+// which grows the disc.
+#pragma once
+
+#include "vor_cells_thread.cuh"
+
+namespace vor {
+
+constexpr int P_NT = 64, P_CMAX = 44, P_SMAX = 16, P_EMAX = 32, P_RMAX = 32;
+constexpr int P_GMAX = P_CMAX - 4;   // sites per gathered list
+constexpr int P_REFILL = 8;          // idle lanes that trigger a batched refill
+
+struct GatherOut {
+    int *count;        // sites in the disc per sorted position (-1: more than P_GMAX)
+    long long *rho2;   // squared disc radius per sorted position
+    int *pos;          // P_GMAX sorted positions per cell
+};
+
+__global__ void __launch_bounds__(256) gather_kernel(CellParams P, GatherOut G) {
+    if (P.hdr->err) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.n) return;
+    const int2 p = P.sxy[i];
+    const int s = P.s;
+    const int bx = p.x / s, by = p.y / s;
+    int c9 = 0, nb9 = 0;
+    {
+        const int x0 = max(bx - 1, 0), x1 = min(bx + 1, P.m1 - 1);
+        for (int row = max(by - 1, 0); row <= min(by + 1, P.m2 - 1); row++) {
+            c9 += P.bstart[row * P.m1 + x1 + 1] - P.bstart[row * P.m1 + x0];
+            nb9 += x1 - x0 + 1;
+        }
+    }
+    const float area = (float)nb9 * (float)s * (float)s;
+    i64 rho2 = (i64)((float)P.target * area / (3.14159265f * (float)max(c9 - 1, 1)));
+    rho2 = max(min(rho2, (i64)(16.f * (float)s * (float)s)), (i64)4);
+    const int r = (int)ceilf(sqrtf((float)rho2)) + 1;
+    const int bx0 = p.x - r <= 0 ? 0 : (p.x - r) / s, bx1 = min(P.m1 - 1, (p.x + r) / s);
+    const int by0 = p.y - r <= 0 ? 0 : (p.y - r) / s, by1 = min(P.m2 - 1, (p.y + r) / s);
+    int cnt = 0;
+    int *dst = G.pos + (size_t)i * P_GMAX;
+    for (int row = by0; row <= by1; row++) {
+        const int a = P.bstart[row * P.m1 + bx0], b = P.bstart[row * P.m1 + bx1 + 1];
+        for (int pos = a; pos < b; pos++) {
+            if (pos == i) continue;
+            const int2 q = P.sxy[pos];
+            const int nx = q.x - p.x, ny = q.y - p.y;
+            if ((i64)nx * nx + (i64)ny * ny > rho2) continue;
+            if (cnt < P_GMAX) dst[cnt] = pos;
+            cnt++;
+        }
+    }
+    G.count[i] = cnt > P_GMAX ? -1 : cnt;
+    G.rho2[i] = rho2;
+}
+
+template <int NT, int CMAX, int SMAX, int EMAX, int RMAX>
+__global__ void __launch_bounds__(NT) cells_persist_kernel(CellParams P, GatherOut G) {
+    extern __shared__ __align__(16) float4 tbl_raw[];
+    if (P.hdr->err) return;
+    const t1::Table<NT> T{tbl_raw + threadIdx.x};
+    const unsigned FULL = 0xffffffffu;
+    int cpos[CMAX];
+    long long stx[SMAX], sty[SMAX];
+    unsigned char scw[SMAX], sccw[SMAX];
+    unsigned char emit[EMAX];
+    t1::Counters cnt{};
+    const int stride = gridDim.x * NT;
+    int t = blockIdx.x * NT + threadIdx.x;
+
+    // state of the thread's current cell
+    int i = -1, C = 0;
+    int2 p = make_int2(0, 0);
+    i64 rho2 = 0;
+    int phase = 0, h0c = -1, h0w = -1, h1c = -1, h1w = -1;
+    i64 lx = 0, ly = 0;
+    int llab = -1, sp = 0, ne = 0, rays = 3, first = -1, last = -1;
+    bool have = false;     // a cell is loaded and its projector runs
+    bool fin = false;      // the projector finished: certificate and output pending
+    bool ok = true;        // the projector stayed within the capacities
+    bool retired = false;  // no cells left for this thread
+
+    for (;;) {
+        // ---- batched finalise + load ------------------------------------------
+        const bool idle = !have && !retired;
+        const unsigned idlem = __ballot_sync(FULL, idle);
+        const unsigned busym = __ballot_sync(FULL, have);
+        if (idlem != 0 && (__popc(idlem) >= P_REFILL || busym == 0)) {
+            if (idle) {
+                if (fin) {
+                    fin = false;
+                    bool defer = !ok;
+                    int e = ne;
+                    if (!defer) {
+                        if (e > 1 && last == first) e--;           // the walk closes
+                        if (e < 3) defer = true;
+                    }
+                    if (!defer) {
+                        // security-radius certificate: 2R <= rho
+                        float R2 = 0.f;
+                        for (int q = 0; q < e; q++) {
+                            int n1x, n1y, n2x, n2y;
+                            i64 c1, c2, Nx, Ny, D;
+                            T.line(emit[q], n1x, n1y, c1);
+                            T.line(emit[q + 1 < e ? q + 1 : 0], n2x, n2y, c2);
+                            intersect(n1x, n1y, c1, n2x, n2y, c2, Nx, Ny, D);
+                            if (D == 0) { defer = true; break; }
+                            const float rd = 1.f / (float)D;
+                            const float vx = (float)Nx * rd, vy = (float)Ny * rd;
+                            R2 = fmaxf(R2, fmaf(vx, vx, vy * vy));
+                        }
+                        const i64 cxf = max(p.x, P.W - p.x), cyf = max(p.y, P.H - p.y);
+                        const i64 need = (i64)(4.f * (R2 * (1.f + 0x1p-12f) + 1.f)) + 1;
+                        if (!(need <= rho2 || rho2 >= cxf * cxf + cyf * cyf)) defer = true;
+                    }
+                    if (!defer) {
+                        // canonical order: start at the smallest normal angle
+                        int start = 0, bxn, byn, qx, qy;
+                        i64 dummy;
+                        T.line(emit[0], bxn, byn, dummy);
+                        for (int q = 1; q < e; q++) {
+                            T.line(emit[q], qx, qy, dummy);
+                            if (angle_less(qx, qy, bxn, byn)) { start = q; bxn = qx; byn = qy; }
+                        }
+                        const int k = P.sid[i];
+                        int *dst;
+                        int off = -1;
+                        if (e <= SLOT_CAP) {
+                            dst = P.slot + (size_t)k * SLOT_CAP;
+                        } else {
+                            off = atomicAdd(&P.hdr->spill_top, e);
+                            if (off + e > P.spill_cap) defer = true;
+                            dst = P.spill + off;
+                        }
+                        if (!defer) {
+                            int dcnt = 0;
+                            for (int q = 0; q < e; q++) {
+                                int qq = start + q;
+                                if (qq >= e) qq -= e;
+                                const int c = emit[qq];
+                                const int l = c < 4 ? -1 - c : P.sid[cpos[c]];
+                                dst[q] = l;
+                                dcnt += l > k ? 1 : 0;
+                            }
+                            P.ecount[k] = e;
+                            P.dcount[k] = dcnt;
+                            P.loc[k] = off;
+                            if ((unsigned long long)e > cnt.maxe) cnt.maxe = e;
+                        }
+                    }
+                    if (defer) {
+                        if (P.deferred) {
+                            const int q = atomicAdd(P.deferred_count, 1);
+                            P.deferred[q] = i;
+                            cnt.deferred++;
+                        } else {
+                            atomicOr(&P.hdr->err, ERRB_CAPACITY);
+                        }
+                    }
+                }
+                // load the next cell of this thread's sequence
+                while (t < P.n) {
+                    i = t;
+                    t += stride;
+                    const int nc = G.count[i];
+                    if (nc < 0) {                                   // disc too crowded
+                        if (P.deferred) {
+                            const int q = atomicAdd(P.deferred_count, 1);
+                            P.deferred[q] = i;
+                            cnt.deferred++;
+                        } else {
+                            atomicOr(&P.hdr->err, ERRB_CAPACITY);
+                        }
+                        continue;
+                    }
+                    p = P.sxy[i];
+                    rho2 = G.rho2[i];
+                    T.put(0, t1::cand_of(0, -p.y, true));
+                    T.put(1, t1::cand_of(P.W - p.x, 0, true));
+                    T.put(2, t1::cand_of(0, P.H - p.y, true));
+                    T.put(3, t1::cand_of(-p.x, 0, true));
+                    const int *src = G.pos + (size_t)i * P_GMAX;
+                    for (int q = 0; q < nc; q++) {
+                        const int pos = src[q];
+                        const int2 a = P.sxy[pos];
+                        T.put(4 + q, t1::cand_of(a.x - p.x, a.y - p.y, false));
+                        cpos[4 + q] = pos;
+                    }
+                    C = nc + 4;
+                    cnt.cands += C;
+                    phase = 0; sp = 0; ne = 0; rays = 3; first = -1; last = -1; llab = -1;
+                    ok = true;
+                    have = true;
+                    break;
+                }
+                if (!have) retired = true;
+            }
+        }
+        if (__ballot_sync(FULL, !retired) == 0) break;
+
+        // ---- choose the next ray of this thread's cell -------------------------
+        bool query = false, utest = false;
+        i64 tx = 0, ty = 0, Nx = 0, Ny = 0, D = 0;
+        int la = -1, lb = -1;
+        if (have) {
+            if (phase < 3) {
+                tx = phase == 0 ? 2 : (phase == 1 ? 0 : -2);
+                ty = phase == 1 ? 1 : -1;
+                query = true;
+            } else {
+                while (sp > 0) {
+                    const int top = sp - 1;
+                    const i64 rx = stx[top], ry = sty[top];
+                    const int rcw = scw[top];
+                    if (llab == rcw) {                           // same line: no vertex
+                        if (llab != last) {
+                            if (ne >= EMAX) { ok = false; sp = 0; break; }
+                            emit[ne++] = (unsigned char)llab;
+                            if (first < 0) first = llab;
+                            last = llab;
+                        }
+                        lx = rx; ly = ry; llab = sccw[top];
+                        sp--;
+                        continue;
+                    }
+                    int n1x, n1y, n2x, n2y;
+                    i64 c1, c2;
+                    T.line(llab, n1x, n1y, c1);
+                    T.line(rcw, n2x, n2y, c2);
+                    intersect(n1x, n1y, c1, n2x, n2y, c2, Nx, Ny, D);
+                    la = llab;
+                    lb = rcw;
+                    if (D == 0) {                                // parallel lines
+                        tx = -(i64)n1y;
+                        ty = (i64)n1x;
+                        if (!(cross128(lx, ly, tx, ty) >= 0 && cross128(tx, ty, rx, ry) >= 0)) {
+                            tx = -tx;
+                            ty = -ty;
+                        }
+                        la = lb = -1;
+                    } else {
+                        const int sg = D > 0 ? 1 : -1;
+                        const bool inw = sg * t1::cross_sign(lx, ly, Nx, Ny) >= 0 &&
+                                         sg * t1::cross_sign(Nx, Ny, rx, ry) >= 0;
+                        tx = sg * Nx;
+                        ty = sg * Ny;
+                        if (inw) {
+                            utest = true;                        // the ray towards u
+                        } else {
+                            tx = -tx;                            // theta_3 := p - u
+                            ty = -ty;
+                            la = lb = -1;
+                        }
+                    }
+                    query = true;
+                    break;
+                }
+                if (!query) { have = false; fin = true; }       // EdgeQueue is empty
+            }
+        }
+
+        // ---- the filter pass (converged across the warp) ------------------------
+        const int Cq = query ? C : 0;
+        const float fx = (float)tx, fy = (float)ty;
+        const float eth = fmaxf(fabsf(fx), fabsf(fy)) * 0x1p-19f;
+        float u1a = -FLT_MAX, u2a = -FLT_MAX, lsa = -FLT_MAX, uxa = -FLT_MAX;
+        float u1b = -FLT_MAX, u2b = -FLT_MAX, lsb = -FLT_MAX, uxb = -FLT_MAX;
+        int i1a = -1, i1b = -1;
+        int c = 0;
+        for (; c + 1 < Cq; c += 2) {
+            const float4 qa = T.get(c), qb = T.get(c + 1);
+            const float da = fmaf(qa.x, fx, qa.y * fy), db = fmaf(qb.x, fx, qb.y * fy);
+            const float ta = qa.w * eth, tb = qb.w * eth;
+            const float Ua = fmaf(da, qa.z, ta), La = fmaf(da, qa.z, -ta);
+            const float Ub = fmaf(db, qb.z, tb), Lb = fmaf(db, qb.z, -tb);
+            if (Ua > u1a) { u2a = u1a; u1a = Ua; i1a = c; lsa = La; } else u2a = fmaxf(u2a, Ua);
+            if (Ub > u1b) { u2b = u1b; u1b = Ub; i1b = c + 1; lsb = Lb; } else u2b = fmaxf(u2b, Ub);
+            if (c != la && c != lb) uxa = fmaxf(uxa, Ua);
+            if (c + 1 != la && c + 1 != lb) uxb = fmaxf(uxb, Ub);
+        }
+        if (c < Cq) {
+            const float4 qa = T.get(c);
+            const float da = fmaf(qa.x, fx, qa.y * fy);
+            const float ta = qa.w * eth;
+            const float Ua = fmaf(da, qa.z, ta), La = fmaf(da, qa.z, -ta);
+            if (Ua > u1a) { u2a = u1a; u1a = Ua; i1a = c; lsa = La; } else u2a = fmaxf(u2a, Ua);
+            if (c != la && c != lb) uxa = fmaxf(uxa, Ua);
+        }
+        if (!query) continue;
+        float u2, ls, ux = fmaxf(uxa, uxb);
+        int i1;
+        if (u1b > u1a || (u1b == u1a && i1b >= 0 && i1b < i1a)) {
+            i1 = i1b; ls = lsb; u2 = fmaxf(fmaxf(u2a, u2b), u1a);
+        } else {
+            i1 = i1a; ls = lsa; u2 = fmaxf(fmaxf(u2a, u2b), u1b);
+        }
+        cnt.evals += C;
+
+        // ---- decide ----------------------------------------------------------
+        int hc = -1, hw = -1;
+        bool inside = false;
+        if (utest) {
+            cnt.vtests++;
+            const i64 aD = D > 0 ? D : -D;
+            const float kuf = (float)(aD / 2);             // key of u: |D|/2, an integer
+            const float klo = kuf * (1.f - 0x1p-21f), khi = kuf * (1.f + 0x1p-21f);
+            if (!P.exact_only && ux < klo) {
+                inside = true;
+            } else if (!P.exact_only && ls > u2 && ls > khi && i1 != la && i1 != lb) {
+                hc = hw = i1;
+            } else {
+                cnt.exact++;
+                bool viol = false;
+                for (int q = 0; q < C && !viol; q++) {
+                    if (q == la || q == lb) continue;
+                    if (!P.exact_only) {
+                        const float4 g = T.get(q);
+                        const float den = fmaf(g.x, fx, g.y * fy);
+                        if (fmaf(den, g.z, g.w * eth) < klo) continue;
+                    }
+                    int nx, ny;
+                    i64 cc;
+                    T.line(q, nx, ny, cc);
+                    const i128 lhs = 2 * dot128(nx, ny, Nx, Ny) * (i128)(D > 0 ? 1 : -1);
+                    if (lhs > (i128)cc * aD) viol = true;
+                }
+                if (!viol) inside = true;
+                else t1::exact_argmax(T, C, tx, ty, fx, fy, eth, !P.exact_only, ls, hc, hw);
+            }
+        } else {
+            cnt.rays++;
+            if (!P.exact_only && ls > u2 && ls > 0.f) {
+                hc = hw = i1;
+            } else {
+                cnt.exact++;
+                t1::exact_argmax(T, C, tx, ty, fx, fy, eth, !P.exact_only, ls, hc, hw);
+            }
+        }
+
+        // ---- update the subedge state ------------------------------------------
+        if (phase < 3) {
+            if (hc < 0) { ok = false; have = false; fin = true; continue; }
+            if (phase == 0) { h0c = hc; h0w = hw; }
+            else if (phase == 1) { h1c = hc; h1w = hw; }
+            else {
+                lx = 2; ly = -1; llab = h0c;
+                stx[0] = 2;  sty[0] = -1; scw[0] = (unsigned char)h0w; sccw[0] = (unsigned char)h0c;
+                stx[1] = -2; sty[1] = -1; scw[1] = (unsigned char)hw;  sccw[1] = (unsigned char)hc;
+                stx[2] = 0;  sty[2] = 1;  scw[2] = (unsigned char)h1w; sccw[2] = (unsigned char)h1c;
+                sp = 3;
+            }
+            phase++;
+        } else if (inside) {                               // u is a vertex: L1, L2 are edges
+            const int top = sp - 1;
+            if (la != last) {
+                if (ne >= EMAX) { ok = false; have = false; fin = true; continue; }
+                emit[ne++] = (unsigned char)la;
+                if (first < 0) first = la;
+                last = la;
+            }
+            if (lb != last) {
+                if (ne >= EMAX) { ok = false; have = false; fin = true; continue; }
+                emit[ne++] = (unsigned char)lb;
+                if (first < 0) first = lb;
+                last = lb;
+            }
+            lx = stx[top]; ly = sty[top]; llab = sccw[top];
+            sp--;
+        } else {                                           // divide the subedge at theta_3
+            if (sp >= SMAX || ++rays > RMAX || hc < 0) { ok = false; have = false; fin = true; continue; }
+            stx[sp] = tx; sty[sp] = ty; scw[sp] = (unsigned char)hw; sccw[sp] = (unsigned char)hc;
+            sp++;
+        }
+    }
+    if (P.collect_stats) {
+        unsigned long long v[10] = {cnt.rays, cnt.vtests, cnt.evals, cnt.exact, cnt.annulus,
+                                    cnt.reruns, cnt.deferred, cnt.cands, cnt.widen, cnt.maxe};
+#pragma unroll
+        for (int q = 0; q < 10; q++) {
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                const unsigned long long o = __shfl_xor_sync(FULL, v[q], off);
+                v[q] = q == 9 ? (o > v[q] ? o : v[q]) : v[q] + o;
+            }
+        }
+        if ((threadIdx.x & 31) == 0) {
+            unsigned long long *st = P.hdr->stats;
+            atomicAdd(&st[STAT_RAYS], v[0]);
+            atomicAdd(&st[STAT_VTESTS], v[1]);
+            atomicAdd(&st[STAT_EVALS], v[2]);
+            atomicAdd(&st[STAT_EXACT], v[3]);
+            atomicAdd(&st[STAT_ANNULUS], v[4]);
+            atomicAdd(&st[STAT_RERUNS], v[5]);
+            atomicAdd(&st[STAT_DEFERRED], v[6]);
+            atomicAdd(&st[STAT_CANDIDATES], v[7]);
+            atomicAdd(&st[STAT_WIDEN], v[8]);
+            atomicMax(&st[STAT_MAXE], v[9]);
+        }
+    }
+}
+
+}  // namespace vor

@@ -1,0 +1,642 @@
+// vor_lib.cu -- bucketing, scans, compaction and the C ABI of libvor.so.
+//
+// Pipeline of one build (all on one stream, no host synchronisation):
+//   K1  bucket_count   validate sites (interior of X, Section 2), count sites
+//                      per bucket of side s (Method A.5), record each site's
+//                      rank inside its bucket
+//       scan           bucket counts -> bucket start offsets
+//       bucket_scatter sites sorted by bucket (row-major), with their index
+//       dup_check      equal sites share a bucket: compare within buckets
+//   K2  cells          the projector per cell (vor_cells.cu), then the
+//                      large-cell pass over the cells it deferred
+//       scan x2        e_k -> cell_ptr, Delaunay counts -> offsets
+//   K3  compact        CSR edge labels, float64 vertices (Section 5) and the
+//                      Delaunay pairs (Section 6)
+#include <cstdio>
+#include <cstring>
+#include <cuda_runtime.h>
+
+#include "vor.h"
+#include "vor_device.cuh"
+#include "vor_internal.h"
+
+namespace vor {
+
+// ---------------------------------------------------------------------------
+// K1: bucketing
+// ---------------------------------------------------------------------------
+
+__global__ void k_bucket_count(const int2 *__restrict__ sites, int n, int W, int H, int s, int m1,
+                               int *__restrict__ bcount, int *__restrict__ rank, WsHeader *hdr) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int2 p = sites[i];
+    if (p.x <= 0 || p.x >= W || p.y <= 0 || p.y >= H) {
+        atomicOr(&hdr->err, ERRB_OUTSIDE);
+        rank[i] = -1;
+        return;
+    }
+    const int b = (p.y / s) * m1 + p.x / s;
+    rank[i] = atomicAdd(&bcount[b], 1);
+}
+
+__global__ void k_bucket_scatter(const int2 *__restrict__ sites, int n, int s, int m1,
+                                 const int *__restrict__ bstart, const int *__restrict__ rank,
+                                 int2 *__restrict__ sxy, int *__restrict__ sid, const WsHeader *hdr) {
+    if (hdr->err) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int2 p = sites[i];
+    const int b = (p.y / s) * m1 + p.x / s;
+    const int pos = bstart[b] + rank[i];
+    sxy[pos] = p;
+    sid[pos] = i;
+}
+
+// Distinct sites (Section 2): equal sites fall into the same bucket, so a
+// comparison inside each bucket finds every duplicate.
+__global__ void k_dup_check(const int2 *__restrict__ sxy, int n, int s, int m1,
+                            const int *__restrict__ bstart, WsHeader *hdr) {
+    if (hdr->err) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int2 p = sxy[i];
+    const int b = (p.y / s) * m1 + p.x / s;
+    const int a = bstart[b], e = bstart[b + 1];
+    for (int j = a; j < e; j++) {
+        if (j == i) continue;
+        const int2 q = sxy[j];
+        if (q.x == p.x && q.y == p.y) { atomicOr(&hdr->err, ERRB_DUPLICATE); return; }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// exclusive scan (reduce -> scan of block sums -> downsweep)
+// ---------------------------------------------------------------------------
+
+constexpr int SCAN_T = 256, SCAN_I = 8, SCAN_TILE = SCAN_T * SCAN_I;
+
+template <class T>
+__device__ T block_exclusive(T v, T *sh, T &total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    T x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        T t = lane < SCAN_T / 32 ? sh[lane] : T(0);
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            T y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < SCAN_T / 32) sh[lane] = t;
+    }
+    __syncthreads();
+    total = sh[SCAN_T / 32 - 1];
+    const T before = w > 0 ? sh[w - 1] : T(0);
+    __syncthreads();
+    return before + x - v;
+}
+
+template <class T>
+__global__ void k_scan_reduce(const int *__restrict__ in, int n, T *__restrict__ partial,
+                              const WsHeader *hdr) {
+    __shared__ T sh[32];
+    if (hdr->err) return;
+    const int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_I;
+    T s = 0;
+#pragma unroll
+    for (int q = 0; q < SCAN_I; q++) s += (base + q < n) ? (T)in[base + q] : T(0);
+    T total;
+    block_exclusive<T>(s, sh, total);
+    if (threadIdx.x == 0) partial[blockIdx.x] = total;
+}
+
+template <class T>
+__global__ void k_scan_partials(T *__restrict__ partial, int nb, const WsHeader *hdr) {
+    __shared__ T sh[32];
+    if (hdr->err) return;
+    T carry = 0;
+    for (int c0 = 0; c0 < nb; c0 += SCAN_T) {
+        const int i = c0 + threadIdx.x;
+        const T v = i < nb ? partial[i] : T(0);
+        T total;
+        const T ex = block_exclusive<T>(v, sh, total);
+        if (i < nb) partial[i] = carry + ex;
+        carry += total;
+    }
+}
+
+// out[i] = sum of in[0..i) for i < n, and out[n] = total; optionally *tot = total.
+template <class T>
+__global__ void k_scan_down(const int *__restrict__ in, int n, const T *__restrict__ partial,
+                            T *__restrict__ out, long long *tot, const WsHeader *hdr) {
+    __shared__ T sh[32];
+    if (hdr->err) return;
+    const int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_I;
+    T v[SCAN_I];
+    T s = 0;
+#pragma unroll
+    for (int q = 0; q < SCAN_I; q++) {
+        v[q] = (base + q < n) ? (T)in[base + q] : T(0);
+        s += v[q];
+    }
+    T total;
+    T run = partial[blockIdx.x] + block_exclusive<T>(s, sh, total);
+#pragma unroll
+    for (int q = 0; q < SCAN_I; q++) {
+        if (base + q < n) out[base + q] = run;
+        run += v[q];
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
+        const T t = partial[blockIdx.x] + total;
+        out[n] = t;
+        if (tot) *tot = (long long)t;
+    }
+}
+
+template <class T>
+static void scan(const int *in, int n, T *out, T *partial, long long *tot, WsHeader *hdr,
+                 cudaStream_t st) {
+    const int nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+    const int nbb = nb > 0 ? nb : 1;
+    k_scan_reduce<T><<<nbb, SCAN_T, 0, st>>>(in, n, partial, hdr);
+    k_scan_partials<T><<<1, SCAN_T, 0, st>>>(partial, nbb, hdr);
+    k_scan_down<T><<<nbb, SCAN_T, 0, st>>>(in, n, partial, out, tot, hdr);
+}
+
+// ---------------------------------------------------------------------------
+// K3: compaction (CSR cells, float64 vertices, Delaunay pairs)
+// ---------------------------------------------------------------------------
+
+struct CompactParams {
+    const int2 *sites;
+    int n, W, H;
+    const int *ecount, *dcount, *loc, *slot, *spill;
+    const long long *cell_ptr, *del_ptr;
+    int *edge_label;
+    double *vx, *vy;
+    int *del_edge;
+    long long edge_cap, del_cap;
+    WsHeader *hdr;
+};
+
+// line of label `lab` of the cell of p: 2 <n, v - p> = c
+__device__ __forceinline__ void line_of(const int2 *sites, int W, int H, int2 p, int lab, int &nx,
+                                        int &ny, i64 &c) {
+    if (lab >= 0) {
+        const int2 a = sites[lab];
+        nx = a.x - p.x;
+        ny = a.y - p.y;
+        c = (i64)nx * nx + (i64)ny * ny;
+    } else {
+        nx = ny = 0;
+        if (lab == VOR_SIDE_BOTTOM) ny = -p.y;
+        else if (lab == VOR_SIDE_RIGHT) nx = W - p.x;
+        else if (lab == VOR_SIDE_TOP) ny = H - p.y;
+        else nx = -p.x;
+        c = 2 * ((i64)nx * nx + (i64)ny * ny);
+    }
+}
+
+__global__ void k_compact(CompactParams Q) {
+    if (Q.hdr->err) return;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= Q.n) return;
+    const int e = Q.ecount[k];
+    const long long off = Q.cell_ptr[k], doff = Q.del_ptr[k];
+    if (off + e > Q.edge_cap || doff + Q.dcount[k] > Q.del_cap) {
+        atomicOr(&Q.hdr->err, ERRB_SPILL);
+        return;
+    }
+    const int l = Q.loc[k];
+    const int *src = l < 0 ? Q.slot + (size_t)k * SLOT_CAP : Q.spill + l;
+    const int2 p = Q.sites[k];
+    int lab0 = src[0];
+    int n0x, n0y;
+    i64 c0;
+    line_of(Q.sites, Q.W, Q.H, p, lab0, n0x, n0y, c0);
+    int ax = n0x, ay = n0y, a_lab = lab0;
+    i64 ac = c0;
+    for (int q = 0; q < e; q++) {
+        int bx, by, b_lab;
+        i64 bc;
+        if (q + 1 < e) {
+            b_lab = src[q + 1];
+            line_of(Q.sites, Q.W, Q.H, p, b_lab, bx, by, bc);
+        } else {
+            b_lab = lab0; bx = n0x; by = n0y; bc = c0;
+        }
+        i64 Nx, Ny, D;
+        intersect(ax, ay, ac, bx, by, bc, Nx, Ny, D);
+        // absolute vertex (p D + N) / D; the numerators lie in [0, W |D|]
+        const i64 numx = (i64)((unsigned long long)p.x * (unsigned long long)D + (unsigned long long)Nx);
+        const i64 numy = (i64)((unsigned long long)p.y * (unsigned long long)D + (unsigned long long)Ny);
+        Q.edge_label[off + q] = a_lab;
+        Q.vx[off + q] = (double)numx / (double)D;
+        Q.vy[off + q] = (double)numy / (double)D;
+        // Delaunay pair (k, a) for a > k at rank = number of smaller such labels
+        if (a_lab > k) {
+            int rank = 0;
+            for (int r = 0; r < e; r++) {
+                const int o = src[r];
+                rank += (o > k && o < a_lab) ? 1 : 0;
+            }
+            Q.del_edge[2 * (doff + rank)] = k;
+            Q.del_edge[2 * (doff + rank) + 1] = a_lab;
+        }
+        ax = bx; ay = by; ac = bc; a_lab = b_lab;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+struct Layout {
+    int s, m1, m2, lanes, target;
+    size_t hdr, bstart, rank, sxy, sid, partial, ecount, dcount, loc, del_ptr, slot, spill,
+        deferred, deferred2, gcount, grho2, gpos, total;
+    int spill_cap;
+    int n_partial;
+};
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static long long isqrt_floor(long long v) {
+    if (v <= 0) return 0;
+    long long r = (long long)__builtin_sqrt((double)v);
+    while (r * r > v) r--;
+    while ((r + 1) * (r + 1) <= v) r++;
+    return r;
+}
+
+static bool resolve(int64_t n, vor_box box, const vor_opts *o, Layout &L) {
+    if (n < 1 || n > (1 << 27)) return false;
+    if (box.w < 2 || box.h < 2 || box.w > (1 << 20) || box.h > (1 << 20)) return false;
+    vor_opts d;
+    vor_opts_default(&d);
+    if (!o) o = &d;
+    // bucket side: about 2 sites per bucket on average for uniform sites
+    if (o->bucket_side > 0) {
+        if (o->bucket_side > (1 << 20)) return false;
+        L.s = o->bucket_side;
+    } else {
+        const long long area = (long long)box.w * box.h;
+        long long side = isqrt_floor(2 * area / n);
+        if (side < 1) side = 1;
+        if (side > (1 << 20)) side = 1 << 20;
+        L.s = (int)side;
+    }
+    L.m1 = (box.w + L.s - 1) / L.s;
+    L.m2 = (box.h + L.s - 1) / L.s;
+    if ((long long)L.m1 * L.m2 > (1ll << 28)) return false;
+    L.lanes = o->lanes_per_cell > 0 ? o->lanes_per_cell : 1;
+    if (L.lanes != 1 && L.lanes != 2 && L.lanes != 4 && L.lanes != 8 && L.lanes != 16 && L.lanes != 32) return false;
+    L.target = o->target > 0 ? o->target : 22;
+    if (L.target > 40) return false;
+    const size_t m = (size_t)L.m1 * L.m2;
+    const size_t nn = (size_t)n;
+    const int nb_b = (int)((m + SCAN_TILE - 1) / SCAN_TILE), nb_n = (int)((nn + SCAN_TILE - 1) / SCAN_TILE);
+    L.n_partial = (nb_b > nb_n ? nb_b : nb_n) + 1;
+    L.spill_cap = (int)(nn * 10 < (1u << 30) ? nn * 10 : (1u << 30));
+    size_t at = 0;
+    L.hdr = at;      at = align256(at + 256);
+    L.bstart = at;   at = align256(at + (m + 1) * 4);
+    L.rank = at;     at = align256(at + nn * 4);
+    L.sxy = at;      at = align256(at + nn * 8);
+    L.sid = at;      at = align256(at + nn * 4);
+    L.partial = at;  at = align256(at + (size_t)L.n_partial * 8);
+    L.ecount = at;   at = align256(at + nn * 4);
+    L.dcount = at;   at = align256(at + nn * 4);
+    L.loc = at;      at = align256(at + nn * 4);
+    L.del_ptr = at;  at = align256(at + (nn + 1) * 8);
+    L.slot = at;     at = align256(at + nn * SLOT_CAP * 4);
+    L.spill = at;    at = align256(at + (size_t)L.spill_cap * 4);
+    L.deferred = at; at = align256(at + nn * 4);
+    L.deferred2 = at; at = align256(at + nn * 4);
+    L.gcount = at;   at = align256(at + nn * 4);
+    L.grho2 = at;    at = align256(at + nn * 8);
+    L.gpos = at;     at = align256(at + nn * 4 * (size_t)first_pass_gather_width());
+    L.total = at;
+    return true;
+}
+
+// stage timing (vor_stage_timing / vor_stage_ms)
+static bool g_timing = false;
+static cudaEvent_t g_ev[5];
+static bool g_ev_made = false;
+static bool g_ev_recorded = false;
+
+static void mark(int i, cudaStream_t st) {
+    if (g_timing) cudaEventRecord(g_ev[i], st);
+}
+
+static int launch_build(const vor_site *d_sites, int64_t n64, vor_box box, const vor_opts *o,
+                        void *ws, const Layout &L, const vor_out *out, cudaStream_t st) {
+    vor_opts d;
+    vor_opts_default(&d);
+    if (!o) o = &d;
+    const int n = (int)n64;
+    char *base = (char *)ws;
+    WsHeader *hdr = (WsHeader *)(base + L.hdr);
+    int *bstart = (int *)(base + L.bstart);
+    int *rank = (int *)(base + L.rank);
+    int2 *sxy = (int2 *)(base + L.sxy);
+    int *sid = (int *)(base + L.sid);
+    long long *partial = (long long *)(base + L.partial);
+    int *ecount = (int *)(base + L.ecount);
+    int *dcount = (int *)(base + L.dcount);
+    int *loc = (int *)(base + L.loc);
+    long long *del_ptr = (long long *)(base + L.del_ptr);
+    int *slot = (int *)(base + L.slot);
+    int *spill = (int *)(base + L.spill);
+    int *deferred = (int *)(base + L.deferred);
+    int *deferred2 = (int *)(base + L.deferred2);
+    const int2 *sites = (const int2 *)d_sites;
+    const int m = L.m1 * L.m2;
+
+    mark(0, st);
+    if (cudaMemsetAsync(hdr, 0, 256, st) != cudaSuccess) return VOR_E_CUDA;
+    if (cudaMemsetAsync(bstart, 0, (size_t)(m + 1) * 4, st) != cudaSuccess) return VOR_E_CUDA;
+    const int T = 256;
+    const int gn = (n + T - 1) / T;
+    k_bucket_count<<<gn, T, 0, st>>>(sites, n, box.w, box.h, L.s, L.m1, bstart, rank, hdr);
+    scan<int>(bstart, m, bstart, (int *)partial, nullptr, hdr, st);
+    k_bucket_scatter<<<gn, T, 0, st>>>(sites, n, L.s, L.m1, bstart, rank, sxy, sid, hdr);
+    if (o->check_duplicates) k_dup_check<<<gn, T, 0, st>>>(sxy, n, L.s, L.m1, bstart, hdr);
+    if (cudaGetLastError() != cudaSuccess) return VOR_E_CUDA;
+    mark(1, st);
+
+    CellParams P;
+    memset(&P, 0, sizeof(P));
+    P.sites = sites; P.sxy = sxy; P.sid = sid; P.bstart = bstart;
+    P.n = n; P.W = box.w; P.H = box.h; P.s = L.s; P.m1 = L.m1; P.m2 = L.m2;
+    P.target = L.target; P.exact_only = o->exact_only; P.collect_stats = o->collect_stats;
+    P.ecount = ecount; P.dcount = dcount; P.loc = loc; P.slot = slot; P.spill = spill;
+    P.spill_cap = L.spill_cap;
+    P.cell_list = nullptr; P.list_count = nullptr; P.n_list = 0;
+    P.hdr = hdr;
+    if (L.lanes == 1) {
+        // first pass: one thread per cell, no certificate widening
+        P.deferred = deferred;
+        P.deferred_count = &hdr->ndeferred;
+        if (launch_cells_first_pass(P, (int *)(base + L.gcount), (long long *)(base + L.grho2),
+                                    (int *)(base + L.gpos), st) != cudaSuccess)
+            return VOR_E_CUDA;
+        mark(2, st);
+        // second pass over the cells the first disc did not certify
+        CellParams P2 = P;
+        P2.cell_list = deferred;
+        P2.list_count = &hdr->ndeferred;
+        P2.n_list = n;
+        P2.deferred = deferred2;
+        P2.deferred_count = &hdr->ndeferred2;
+        if (launch_cells_thread(P2, true, st) != cudaSuccess) return VOR_E_CUDA;
+    } else {
+        P.deferred = deferred2;
+        P.deferred_count = &hdr->ndeferred2;
+        if (launch_cells_fast(P, L.lanes, st) != cudaSuccess) return VOR_E_CUDA;
+        mark(2, st);
+    }
+    // warp per cell, large capacities, for what is left
+    CellParams PL = P;
+    PL.cell_list = deferred2;
+    PL.list_count = &hdr->ndeferred2;
+    PL.n_list = n;
+    PL.deferred = nullptr;
+    PL.deferred_count = nullptr;
+    if (launch_cells_large(PL, n, st) != cudaSuccess) return VOR_E_CUDA;
+    mark(3, st);
+
+    scan<long long>(ecount, n, (long long *)out->cell_ptr, partial, (long long *)out->totals, hdr, st);
+    scan<long long>(dcount, n, del_ptr, partial, (long long *)out->totals + 1, hdr, st);
+    CompactParams Q;
+    Q.sites = sites; Q.n = n; Q.W = box.w; Q.H = box.h;
+    Q.ecount = ecount; Q.dcount = dcount; Q.loc = loc; Q.slot = slot; Q.spill = spill;
+    Q.cell_ptr = (const long long *)out->cell_ptr; Q.del_ptr = del_ptr;
+    Q.edge_label = out->edge_label; Q.vx = out->vx; Q.vy = out->vy; Q.del_edge = out->del_edge;
+    Q.edge_cap = out->edge_cap; Q.del_cap = out->del_cap; Q.hdr = hdr;
+    k_compact<<<gn, T, 0, st>>>(Q);
+    if (cudaGetLastError() != cudaSuccess) return VOR_E_CUDA;
+    mark(4, st);
+    if (g_timing) g_ev_recorded = true;
+    return VOR_OK;
+}
+
+static int map_err(unsigned e) {
+    if (e & ERRB_OUTSIDE) return VOR_E_SITE_OUTSIDE;
+    if (e & ERRB_DUPLICATE) return VOR_E_DUPLICATE;
+    if (e & ERRB_INTERNAL) return VOR_E_INTERNAL;
+    if (e & ERRB_CAPACITY) return VOR_E_CAPACITY;
+    if (e & ERRB_SPILL) return VOR_E_OOM;
+    return VOR_OK;
+}
+
+}  // namespace vor
+
+using namespace vor;
+
+extern "C" {
+
+void vor_opts_default(vor_opts *o) {
+    if (!o) return;
+    o->bucket_side = 0;
+    o->lanes_per_cell = 0;
+    o->target = 0;
+    o->exact_only = 0;
+    o->check_duplicates = 1;
+    o->collect_stats = 0;
+}
+
+int64_t vor_edge_capacity(int64_t n) { return n < 1 ? 0 : 10 * n + 4; }
+int64_t vor_delaunay_capacity(int64_t n) { return n < 3 ? 1 : 3 * n; }
+
+int64_t vor_workspace_bytes(int64_t n, vor_box box, const vor_opts *opts) {
+    Layout L;
+    if (!resolve(n, box, opts, L)) return -1;
+    return (int64_t)L.total;
+}
+
+int vor_build_async(const vor_site *d_sites, int64_t n, vor_box box, const vor_opts *opts,
+                    void *d_workspace, int64_t ws_bytes, const vor_out *out, void *stream) {
+    if (!d_sites || !d_workspace || !out || !out->cell_ptr || !out->edge_label || !out->vx ||
+        !out->vy || !out->del_edge || !out->totals)
+        return VOR_E_INVALID_ARG;
+    if (box.w < 2 || box.h < 2 || box.w > (1 << 20) || box.h > (1 << 20)) return VOR_E_BOX_TOO_LARGE;
+    Layout L;
+    if (!resolve(n, box, opts, L)) return VOR_E_INVALID_ARG;
+    if (ws_bytes < (int64_t)L.total || ((uintptr_t)d_workspace & 255)) return VOR_E_OOM;
+    if (out->edge_cap < 1 || out->del_cap < 1) return VOR_E_OOM;
+    return launch_build(d_sites, n, box, opts, d_workspace, L, out, (cudaStream_t)stream);
+}
+
+int vor_status(const void *d_workspace, void *stream, vor_stats *stats) {
+    if (!d_workspace) return VOR_E_INVALID_ARG;
+    WsHeader h;
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return VOR_E_CUDA;
+    if (cudaMemcpy(&h, d_workspace, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return VOR_E_CUDA;
+    if (stats) {
+        memset(stats, 0, sizeof(*stats));
+        stats->rays = h.stats[STAT_RAYS];
+        stats->vertex_tests = h.stats[STAT_VTESTS];
+        stats->evals = h.stats[STAT_EVALS];
+        stats->exact_rays = h.stats[STAT_EXACT];
+        stats->annulus_sites = h.stats[STAT_ANNULUS];
+        stats->reruns = h.stats[STAT_RERUNS];
+        stats->deferred = h.stats[STAT_DEFERRED];
+        stats->candidates = h.stats[STAT_CANDIDATES];
+        stats->max_edges = h.stats[STAT_MAXE];
+        stats->widenings = h.stats[STAT_WIDEN];
+    }
+    return map_err(h.err);
+}
+
+int vor_build(const vor_site *d_sites, int64_t n, vor_box box, const vor_opts *opts, void *stream,
+              vor_out *out, int64_t *n_edges, int64_t *n_del, vor_stats *stats) {
+    if (!out) return VOR_E_INVALID_ARG;
+    memset(out, 0, sizeof(*out));
+    const int64_t ws = vor_workspace_bytes(n, box, opts);
+    if (ws < 0) return VOR_E_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    void *w = nullptr;
+    out->edge_cap = vor_edge_capacity(n);
+    out->del_cap = vor_delaunay_capacity(n);
+    if (cudaMalloc(&w, (size_t)ws) != cudaSuccess ||
+        cudaMalloc((void **)&out->cell_ptr, (size_t)(n + 1) * 8) != cudaSuccess ||
+        cudaMalloc((void **)&out->edge_label, (size_t)out->edge_cap * 4) != cudaSuccess ||
+        cudaMalloc((void **)&out->vx, (size_t)out->edge_cap * 8) != cudaSuccess ||
+        cudaMalloc((void **)&out->vy, (size_t)out->edge_cap * 8) != cudaSuccess ||
+        cudaMalloc((void **)&out->del_edge, (size_t)out->del_cap * 8) != cudaSuccess ||
+        cudaMalloc((void **)&out->totals, 16) != cudaSuccess) {
+        cudaFree(w);
+        vor_free_result(out, stream);
+        return VOR_E_OOM;
+    }
+    int rc = vor_build_async(d_sites, n, box, opts, w, ws, out, stream);
+    if (rc == VOR_OK) rc = vor_status(w, stream, stats);
+    if (rc == VOR_OK) {
+        int64_t t[2];
+        if (cudaMemcpyAsync(t, out->totals, 16, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            rc = VOR_E_CUDA;
+        if (n_edges) *n_edges = t[0];
+        if (n_del) *n_del = t[1];
+    }
+    cudaStreamSynchronize(st);
+    cudaFree(w);
+    if (rc != VOR_OK) vor_free_result(out, stream);
+    return rc;
+}
+
+int vor_free_result(vor_out *out, void *stream) {
+    if (!out) return VOR_E_INVALID_ARG;
+    cudaStreamSynchronize((cudaStream_t)stream);
+    cudaFree(out->cell_ptr);
+    cudaFree(out->edge_label);
+    cudaFree(out->vx);
+    cudaFree(out->vy);
+    cudaFree(out->del_edge);
+    cudaFree(out->totals);
+    memset(out, 0, sizeof(*out));
+    return VOR_OK;
+}
+
+int64_t vor_host_scratch_bytes(int64_t n) {
+    if (n < 1) return -1;
+    size_t at = 0;
+    at = align256(at + (size_t)n * 8);                          // sites
+    at = align256(at + (size_t)(n + 1) * 8);                    // cell_ptr
+    at = align256(at + (size_t)vor_edge_capacity(n) * 4);       // labels
+    at = align256(at + (size_t)vor_edge_capacity(n) * 8);       // vx
+    at = align256(at + (size_t)vor_edge_capacity(n) * 8);       // vy
+    at = align256(at + (size_t)vor_delaunay_capacity(n) * 8);   // del
+    at = align256(at + 16);                                     // totals
+    return (int64_t)at;
+}
+
+int vor_build_host(const vor_site *h_sites, int64_t n, vor_box box, const vor_opts *opts,
+                   void *d_workspace, int64_t ws_bytes, void *d_scratch, int64_t scratch_bytes,
+                   int64_t *h_cell_ptr, int32_t *h_edge_label, double *h_vx, double *h_vy,
+                   int32_t *h_del_edge, int64_t edge_cap, int64_t del_cap, int64_t *n_edges,
+                   int64_t *n_del, void *stream) {
+    if (!h_sites || !d_scratch || !h_cell_ptr || !h_edge_label || !h_vx || !h_vy || !h_del_edge)
+        return VOR_E_INVALID_ARG;
+    if (n < 1) return VOR_E_INVALID_ARG;
+    if (scratch_bytes < vor_host_scratch_bytes(n) || ((uintptr_t)d_scratch & 255)) return VOR_E_OOM;
+    cudaStream_t st = (cudaStream_t)stream;
+    char *b = (char *)d_scratch;
+    size_t at = 0;
+    vor_site *d_sites = (vor_site *)(b + at); at = align256(at + (size_t)n * 8);
+    vor_out o;
+    o.cell_ptr = (int64_t *)(b + at); at = align256(at + (size_t)(n + 1) * 8);
+    o.edge_label = (int32_t *)(b + at); at = align256(at + (size_t)vor_edge_capacity(n) * 4);
+    o.vx = (double *)(b + at); at = align256(at + (size_t)vor_edge_capacity(n) * 8);
+    o.vy = (double *)(b + at); at = align256(at + (size_t)vor_edge_capacity(n) * 8);
+    o.del_edge = (int32_t *)(b + at); at = align256(at + (size_t)vor_delaunay_capacity(n) * 8);
+    o.totals = (int64_t *)(b + at);
+    o.edge_cap = vor_edge_capacity(n);
+    o.del_cap = vor_delaunay_capacity(n);
+    if (cudaMemcpyAsync(d_sites, h_sites, (size_t)n * 8, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return VOR_E_CUDA;
+    int rc = vor_build_async(d_sites, n, box, opts, d_workspace, ws_bytes, &o, stream);
+    if (rc != VOR_OK) return rc;
+    int64_t t[2] = {0, 0};
+    if (cudaMemcpyAsync(t, o.totals, 16, cudaMemcpyDeviceToHost, st) != cudaSuccess) return VOR_E_CUDA;
+    rc = vor_status(d_workspace, stream, nullptr);
+    if (rc != VOR_OK) return rc;
+    if (t[0] > edge_cap || t[1] > del_cap) return VOR_E_OOM;
+    if (cudaMemcpyAsync(h_cell_ptr, o.cell_ptr, (size_t)(n + 1) * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(h_edge_label, o.edge_label, (size_t)t[0] * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(h_vx, o.vx, (size_t)t[0] * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(h_vy, o.vy, (size_t)t[0] * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(h_del_edge, o.del_edge, (size_t)t[1] * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return VOR_E_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return VOR_E_CUDA;
+    if (n_edges) *n_edges = t[0];
+    if (n_del) *n_del = t[1];
+    return VOR_OK;
+}
+
+int vor_stage_timing(int enable) {
+    if (enable && !g_ev_made) {
+        for (int i = 0; i < 5; i++)
+            if (cudaEventCreate(&g_ev[i]) != cudaSuccess) return VOR_E_CUDA;
+        g_ev_made = true;
+    }
+    g_timing = enable != 0;
+    g_ev_recorded = false;
+    return VOR_OK;
+}
+
+int vor_stage_ms(float *ms, int max_stages) {
+    if (!ms || max_stages < 1) return VOR_E_INVALID_ARG;
+    if (!g_ev_made || !g_ev_recorded) return VOR_E_INVALID_ARG;
+    if (cudaEventSynchronize(g_ev[4]) != cudaSuccess) return VOR_E_CUDA;
+    int k = 0;
+    for (int i = 0; i < 4 && k < max_stages; i++, k++)
+        if (cudaEventElapsedTime(&ms[i], g_ev[i], g_ev[i + 1]) != cudaSuccess) return VOR_E_CUDA;
+    return k;
+}
+
+const char *vor_strerror(int code) {
+    switch (code) {
+    case VOR_OK: return "ok";
+    case VOR_E_INVALID_ARG: return "invalid argument";
+    case VOR_E_SITE_OUTSIDE: return "a site lies on or outside the boundary of the box";
+    case VOR_E_DUPLICATE: return "two sites are equal";
+    case VOR_E_BOX_TOO_LARGE: return "box side outside [2, 2^20]";
+    case VOR_E_OOM: return "workspace or output buffer too small, or out of memory";
+    case VOR_E_CAPACITY: return "a cell exceeded the large-cell capacity";
+    case VOR_E_CUDA: return "CUDA runtime error";
+    case VOR_E_INTERNAL: return "internal consistency check failed";
+    default: return "unknown error";
+    }
+}
+
+}  // extern "C"

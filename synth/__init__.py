@@ -285,3 +285,44 @@ def poisson_requests(n_req: int, rate_per_s: float, seed: int = SEED_BASE + 5,
     sizes = np.floor(np.exp(np.log(lo) + w * (np.log(hi) - np.log(lo)))).astype(np.int64)
     kind = (splitmix64(seed, 32, n_req) >> np.uint64(63)).astype(np.int64)
     return arrivals, np.clip(sizes, lo, hi), kind
+
+
+# ------------------------------------------------------------------ workloads
+
+def _cache_dir():
+    import os
+    import tempfile
+    d = os.path.join(tempfile.gettempdir(), "vor_synth_cache")
+    os.makedirs(d, exist_ok=True)
+    return d
+
+
+def workload(name: str, cache: bool = True) -> np.ndarray:
+    """The named site sets of the benchmark and the parity tests.
+
+    ``uniform_1k``  n = 1,000 uniform sites, no four on an empty circle
+    ``uniform_1m``  n = 1,048,576 uniform sites, no four on an empty circle
+    ``gauss_4m``    n = 4,194,304 sites of the 64-component Gaussian mixture
+                    (sigma = 2^12, Dirichlet(1) weights); co-circular sites allowed
+    All live in the world X = [0, 2^20]^2.
+    """
+    import os
+    spec = {
+        "uniform_1k": (1000, "u", True, SEED_BASE + 1),
+        "uniform_1m": (1 << 20, "u", True, SEED_BASE + 2),
+        "gauss_4m": (1 << 22, "g", False, SEED_BASE + 3),
+    }
+    n, kind, gp, seed = spec[name]
+    path = os.path.join(_cache_dir(), f"{name}_{seed}.npy") if cache else None
+    if path and os.path.exists(path):
+        xy = np.load(path)
+        if xy.shape == (n, 2):
+            return xy
+    xy = uniform_sites(n, seed=seed) if kind == "u" else gaussian_mixture_sites(n, seed=seed)
+    if gp:
+        xy = enforce_general_position(xy, seed=seed)
+    if path:
+        tmp = path + f".{os.getpid()}.npy"
+        np.save(tmp, xy)
+        os.replace(tmp, path)
+    return xy

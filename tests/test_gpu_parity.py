@@ -1,0 +1,120 @@
+"""GPU parity: the CUDA path (through the C ABI) against the exact oracle.
+
+Combinatorial output (cell offsets, edge labels in canonical order, Delaunay
+pairs) must be bit-identical; float64 vertices within 1e-9 relative of the
+oracle's exact rationals.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from parity import (assert_full_parity, assert_sampled_parity, delaunay_symmetric_ok, to_numpy)
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1212_1095_gb300 as vg  # noqa: E402
+
+BOX = 1 << 20
+
+
+def gpu(xy, box, **opts):
+    t = torch.from_numpy(np.ascontiguousarray(xy, dtype=np.int32)).cuda()
+    return to_numpy(vg.build(t, box, **opts))
+
+
+# ----------------------------------------------------------- closed forms
+
+def test_single_site():
+    d = gpu(np.array([[300, 700]]), (1000, 800))
+    assert d["labels"].tolist() == [-2, -3, -4, -1]
+    assert d["vx"].tolist() == [1000, 0, 0, 1000] and d["vy"].tolist() == [800, 800, 0, 0]
+    assert d["delaunay"].shape[0] == 0
+
+
+@pytest.mark.parametrize("lanes", [2, 4, 8, 16, 32])
+def test_lattice_and_degenerate_layouts(lanes):
+    cases = [
+        (synth.lattice_sites(7, 20, 10), 140),
+        (np.array([[x, 400] for x in (100, 300, 500, 700)]), 800),
+        (np.array([[1, 3], [3, 1]]), 4),
+        (np.array([[50, 50], [60, 60], [40, 60], [50, 70]]), 100),
+        (synth.lattice_sites(12, 1000, 500), 12000),
+    ]
+    for xy, box in cases:
+        for exact_only in (0, 1):
+            d = gpu(xy, box, lanes_per_cell=lanes, exact_only=exact_only)
+            assert_full_parity(d, oracle.cells(xy, box, "plain"))
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_small_random_sets(seed):
+    n = [1, 2, 3, 5, 8, 13, 40, 77, 150, 333, 512, 999][seed]
+    box = [64, 1000, 4096, 1 << 20][seed % 4]
+    xy = synth.uniform_sites(n, seed=500 + seed, box=box)
+    r = oracle.cells(xy, box, "plain")
+    for lanes in (4, 8, 32):
+        assert_full_parity(gpu(xy, box, lanes_per_cell=lanes), r)
+
+
+def test_uniform_1k_all_variants():
+    # n = 1,000 uniform sites, no four co-circular; every kernel variant
+    xy = synth.workload("uniform_1k")
+    r = oracle.cells(xy, BOX, "plain")
+    assert r["stats"][:, 5].sum() == 0, "general position"
+    for lanes in (2, 4, 8, 16, 32):
+        for target in (6, 20, 40):
+            assert_full_parity(gpu(xy, BOX, lanes_per_cell=lanes, target=target), r)
+    assert_full_parity(gpu(xy, BOX, exact_only=1), r)
+    # tiny buckets force certificate reruns, huge buckets the large-cell pass
+    for side in (2000, 8000, 200000, 1 << 20):
+        assert_full_parity(gpu(xy, BOX, bucket_side=side), r)
+
+
+def test_extreme_coordinates():
+    M = BOX - 1
+    xy = np.array([[1, 1], [M, M], [1, M], [M, 1], [2, 1], [1, 2], [M - 1, M],
+                   [1 << 19, 1 << 19], [(1 << 19) + 1, 1 << 19], [3, M - 5]])
+    assert_full_parity(gpu(xy, BOX), oracle.cells(xy, BOX, "plain"))
+
+
+def test_clustered_medium():
+    xy = synth.gaussian_mixture_sites(60000, seed=4242, sigma=2000.0)
+    r = oracle.cells(xy, BOX, "bucketed")
+    d = gpu(xy, BOX, collect_stats=1)
+    assert_full_parity(d, r)
+
+
+def test_errors_are_reported():
+    with pytest.raises(vg.VorError) as e:
+        gpu(np.array([[0, 5], [3, 4]]), 100)
+    assert e.value.code == -2
+    with pytest.raises(vg.VorError) as e:
+        gpu(np.array([[5, 5], [3, 4], [5, 5]]), 100)
+    assert e.value.code == -3
+    with pytest.raises(vg.VorError) as e:
+        gpu(np.array([[5, 5]]), (1 << 20) + 1)
+    assert e.value.code in (-1, -4)
+    # the context stays usable after device-detected errors
+    d = gpu(np.array([[30, 40], [60, 20]]), 100)
+    assert d["cell_ptr"][-1] > 0
+
+
+def test_uniform_1m_full_parity():
+    # n = 1,048,576 uniform sites (the benchmark workload), whole diagram
+    xy = synth.workload("uniform_1m")
+    d = gpu(xy, BOX, collect_stats=1)
+    r = oracle.cells(xy, BOX, "bucketed")
+    assert r["stats"][:, 5].sum() == 0, "general position"
+    assert_full_parity(d, r)
+    delaunay_symmetric_ok(d, xy.shape[0])
+
+
+def test_host_entry_point_matches_device_entry_point():
+    xy = synth.uniform_sites(20000, seed=99)
+    a = gpu(xy, BOX)
+    b = to_numpy(vg.build_host(xy, BOX))
+    for key in ("cell_ptr", "labels", "vx", "vy", "delaunay"):
+        assert np.array_equal(a[key], b[key]), key
