@@ -353,15 +353,15 @@ template <int G, int CMAX, int SMAX, int EMAX>
 __device__ int scan_disc(const CellParams &P, GroupSmem<CMAX, SMAX, EMAX> &S, const int2 p,
                          const int self, const i64 r2lo, const i64 r2hi, const bool cut_only,
                          const int e, const int cap, const int gl, Counters &cnt) {
-    const int s = P.s;
+    const int s = P.hdr->s;
     const int r = (int)ceilf(sqrtf((float)r2hi)) + 1;
     const int bx0 = p.x - r <= 0 ? 0 : (p.x - r) / s;
-    const int bx1 = min(P.m1 - 1, (p.x + r) / s);
+    const int bx1 = min(P.hdr->m1 - 1, (p.x + r) / s);
     const int by0 = p.y - r <= 0 ? 0 : (p.y - r) / s;
-    const int by1 = min(P.m2 - 1, (p.y + r) / s);
+    const int by1 = min(P.hdr->m2 - 1, (p.y + r) / s);
     int seen = 0;
     for (int row = by0; row <= by1; row++) {
-        const int a = P.bstart[row * P.m1 + bx0], b = P.bstart[row * P.m1 + bx1 + 1];
+        const int a = P.bstart[row * P.hdr->m1 + bx0], b = P.bstart[row * P.hdr->m1 + bx1 + 1];
         seen += b - a;
         for (int pos = a + gl; pos < b; pos += G) {
             if (pos == self) continue;
@@ -443,13 +443,13 @@ __device__ int process_cell(const CellParams &P, GroupSmem<CMAX, SMAX, EMAX> &S,
     // ---- 1. candidates: the sites within rho of p, then the four sides --------
     // rho is chosen so that about P.target sites fall in the disc, from the
     // site density of the 3x3 buckets around p's bucket
-    const int s = P.s;
+    const int s = P.hdr->s;
     const int bx = p.x / s, by = p.y / s;
     int c9 = 0, nb9 = 0;
     {
-        const int x0 = max(bx - 1, 0), x1 = min(bx + 1, P.m1 - 1);
-        for (int row = max(by - 1, 0); row <= min(by + 1, P.m2 - 1); row++) {
-            c9 += P.bstart[row * P.m1 + x1 + 1] - P.bstart[row * P.m1 + x0];
+        const int x0 = max(bx - 1, 0), x1 = min(bx + 1, P.hdr->m1 - 1);
+        for (int row = max(by - 1, 0); row <= min(by + 1, P.hdr->m2 - 1); row++) {
+            c9 += P.bstart[row * P.hdr->m1 + x1 + 1] - P.bstart[row * P.hdr->m1 + x0];
             nb9 += x1 - x0 + 1;
         }
     }
@@ -508,12 +508,19 @@ __device__ int process_cell(const CellParams &P, GroupSmem<CMAX, SMAX, EMAX> &S,
             const i64 nb = (i64)(2 * r / s + 2) * (2 * r / s + 2);
             if (nb * 4 > Limits<LARGE>::scan) return CELL_DEFER;
         }
-        if (gl == 0) S.ncand = C;
-        group_sync<G>(gmask);
-        scanned += scan_disc<G>(P, S, p, i, rho2, rho2n, true, e, CMAX, gl, cnt);
-        rho2 = rho2n;
-        group_sync<G>(gmask);
-        if (S.flag) return CELL_DEFER;
+        i64 step2 = rho2n;
+        for (int shrink = 0;; shrink++) {
+            if (gl == 0) { S.ncand = C; S.flag = 0; }
+            group_sync<G>(gmask);
+            scanned += scan_disc<G>(P, S, p, i, rho2, step2, true, e, CMAX, gl, cnt);
+            group_sync<G>(gmask);
+            if (!S.flag) break;
+            // too many sites cut the polygon at once: test a thinner annulus
+            // first (its cutters shrink the polygon, so fewer cut later)
+            if (!LARGE || shrink >= 40 || step2 <= rho2 + 1) return CELL_DEFER;
+            step2 = rho2 + (step2 - rho2) / 4;
+        }
+        rho2 = step2;
         const int ncut = S.ncand - C;
         if (ncut > 0) {
             cnt.reruns++;

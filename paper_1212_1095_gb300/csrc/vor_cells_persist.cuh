@@ -36,13 +36,13 @@ __global__ void __launch_bounds__(256) gather_kernel(CellParams P, GatherOut G) 
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P.n) return;
     const int2 p = P.sxy[i];
-    const int s = P.s;
+    const int s = P.hdr->s;
     const int bx = p.x / s, by = p.y / s;
     int c9 = 0, nb9 = 0;
     {
-        const int x0 = max(bx - 1, 0), x1 = min(bx + 1, P.m1 - 1);
-        for (int row = max(by - 1, 0); row <= min(by + 1, P.m2 - 1); row++) {
-            c9 += P.bstart[row * P.m1 + x1 + 1] - P.bstart[row * P.m1 + x0];
+        const int x0 = max(bx - 1, 0), x1 = min(bx + 1, P.hdr->m1 - 1);
+        for (int row = max(by - 1, 0); row <= min(by + 1, P.hdr->m2 - 1); row++) {
+            c9 += P.bstart[row * P.hdr->m1 + x1 + 1] - P.bstart[row * P.hdr->m1 + x0];
             nb9 += x1 - x0 + 1;
         }
     }
@@ -50,12 +50,12 @@ __global__ void __launch_bounds__(256) gather_kernel(CellParams P, GatherOut G) 
     i64 rho2 = (i64)((float)P.target * area / (3.14159265f * (float)max(c9 - 1, 1)));
     rho2 = max(min(rho2, (i64)(16.f * (float)s * (float)s)), (i64)4);
     const int r = (int)ceilf(sqrtf((float)rho2)) + 1;
-    const int bx0 = p.x - r <= 0 ? 0 : (p.x - r) / s, bx1 = min(P.m1 - 1, (p.x + r) / s);
-    const int by0 = p.y - r <= 0 ? 0 : (p.y - r) / s, by1 = min(P.m2 - 1, (p.y + r) / s);
+    const int bx0 = p.x - r <= 0 ? 0 : (p.x - r) / s, bx1 = min(P.hdr->m1 - 1, (p.x + r) / s);
+    const int by0 = p.y - r <= 0 ? 0 : (p.y - r) / s, by1 = min(P.hdr->m2 - 1, (p.y + r) / s);
     int cnt = 0;
     int *dst = G.pos + (size_t)i * P_GMAX;
     for (int row = by0; row <= by1; row++) {
-        const int a = P.bstart[row * P.m1 + bx0], b = P.bstart[row * P.m1 + bx1 + 1];
+        const int a = P.bstart[row * P.hdr->m1 + bx0], b = P.bstart[row * P.hdr->m1 + bx1 + 1];
         for (int pos = a; pos < b; pos++) {
             if (pos == i) continue;
             const int2 q = P.sxy[pos];

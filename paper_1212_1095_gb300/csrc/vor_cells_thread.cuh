@@ -292,7 +292,7 @@ template <int NT, int CMAX, int SMAX, int EMAX, int RMAX, bool WIDEN>
 __device__ int cell(const CellParams &P, const Table<NT> &T, int *lab, int i, Counters &cnt) {
     const int2 p = P.sxy[i];
     const int k = P.sid[i];
-    const int s = P.s;
+    const int s = P.hdr->s;
 
     // ---- 1. candidates: the four sides, then the sites within rho of p ------
     {
@@ -308,9 +308,9 @@ __device__ int cell(const CellParams &P, const Table<NT> &T, int *lab, int i, Co
     const int bx = p.x / s, by = p.y / s;
     int c9 = 0, nb9 = 0;
     {
-        const int x0 = max(bx - 1, 0), x1 = min(bx + 1, P.m1 - 1);
-        for (int row = max(by - 1, 0); row <= min(by + 1, P.m2 - 1); row++) {
-            c9 += P.bstart[row * P.m1 + x1 + 1] - P.bstart[row * P.m1 + x0];
+        const int x0 = max(bx - 1, 0), x1 = min(bx + 1, P.hdr->m1 - 1);
+        for (int row = max(by - 1, 0); row <= min(by + 1, P.hdr->m2 - 1); row++) {
+            c9 += P.bstart[row * P.hdr->m1 + x1 + 1] - P.bstart[row * P.hdr->m1 + x0];
             nb9 += x1 - x0 + 1;
         }
     }
@@ -322,10 +322,10 @@ __device__ int cell(const CellParams &P, const Table<NT> &T, int *lab, int i, Co
     int scanned = 0;
     {
         const int r = (int)ceilf(sqrtf((float)rho2)) + 1;
-        const int bx0 = p.x - r <= 0 ? 0 : (p.x - r) / s, bx1 = min(P.m1 - 1, (p.x + r) / s);
-        const int by0 = p.y - r <= 0 ? 0 : (p.y - r) / s, by1 = min(P.m2 - 1, (p.y + r) / s);
+        const int bx0 = p.x - r <= 0 ? 0 : (p.x - r) / s, bx1 = min(P.hdr->m1 - 1, (p.x + r) / s);
+        const int by0 = p.y - r <= 0 ? 0 : (p.y - r) / s, by1 = min(P.hdr->m2 - 1, (p.y + r) / s);
         for (int row = by0; row <= by1; row++) {
-            const int a = P.bstart[row * P.m1 + bx0], b = P.bstart[row * P.m1 + bx1 + 1];
+            const int a = P.bstart[row * P.hdr->m1 + bx0], b = P.bstart[row * P.hdr->m1 + bx1 + 1];
             scanned += b - a;
             for (int pos = a; pos < b; pos++) {
                 if (pos == i) continue;
@@ -368,12 +368,12 @@ __device__ int cell(const CellParams &P, const Table<NT> &T, int *lab, int i, Co
         cnt.widen++;
         const i64 rho2n = min(min(need, 4 * rho2 + 4), far2);
         const int r = (int)ceilf(sqrtf((float)rho2n)) + 1;
-        const int bx0 = p.x - r <= 0 ? 0 : (p.x - r) / s, bx1 = min(P.m1 - 1, (p.x + r) / s);
-        const int by0 = p.y - r <= 0 ? 0 : (p.y - r) / s, by1 = min(P.m2 - 1, (p.y + r) / s);
+        const int bx0 = p.x - r <= 0 ? 0 : (p.x - r) / s, bx1 = min(P.hdr->m1 - 1, (p.x + r) / s);
+        const int by0 = p.y - r <= 0 ? 0 : (p.y - r) / s, by1 = min(P.hdr->m2 - 1, (p.y + r) / s);
         if ((by1 - by0 + 1) * (bx1 - bx0 + 1) > 128) return DEFER;
         const int C0 = C;
         for (int row = by0; row <= by1; row++) {
-            const int a = P.bstart[row * P.m1 + bx0], b = P.bstart[row * P.m1 + bx1 + 1];
+            const int a = P.bstart[row * P.hdr->m1 + bx0], b = P.bstart[row * P.hdr->m1 + bx1 + 1];
             scanned += b - a;
             for (int pos = a; pos < b; pos++) {
                 const int2 q = P.sxy[pos];

@@ -30,7 +30,8 @@ struct WsHeader {
     int ndeferred;          // cells handed from the first to the second pass
     int ndeferred2;         // cells handed to the warp-per-cell pass
     unsigned long long stats[STAT_N];
-    long long pad[12];
+    int s, m1, m2, m;       // bucket side and grid (chosen on the device)
+    long long pad[10];
 };
 static_assert(sizeof(WsHeader) <= 256, "header");
 
@@ -43,8 +44,6 @@ struct CellParams {
     const int *sid;         // original index of sorted position
     const int *bstart;      // bucket CSR (m1*m2 + 1)
     int n, W, H;
-    int s;                  // bucket side
-    int m1, m2;
     int target;             // sites wanted in the first candidate disc
     int exact_only;
     int collect_stats;

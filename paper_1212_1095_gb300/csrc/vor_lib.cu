@@ -26,7 +26,61 @@ namespace vor {
 // K1: bucketing
 // ---------------------------------------------------------------------------
 
-__global__ void k_bucket_count(const int2 *__restrict__ sites, int n, int W, int H, int s, int m1,
+// Site density probe: the bucket side is chosen so that the bucket of the
+// median site (by its own neighbourhood) holds about two sites.  A coarse
+// G x G grid counts the sites; each site reads its coarse cell's count into a
+// log2 histogram; the median bin gives the local density.
+__global__ void k_probe_count(const int2 *__restrict__ sites, int n, int W, int H, int G,
+                              int *__restrict__ coarse) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int2 p = sites[i];
+    if (p.x <= 0 || p.x >= W || p.y <= 0 || p.y >= H) return;   // reported by k_bucket_count
+    const int cx = (int)((long long)p.x * G / W), cy = (int)((long long)p.y * G / H);
+    atomicAdd(&coarse[cy * G + cx], 1);
+}
+
+__global__ void k_probe_hist(const int2 *__restrict__ sites, int n, int W, int H, int G,
+                             const int *__restrict__ coarse, int *__restrict__ hist) {
+    __shared__ int h[32];
+    if (threadIdx.x < 32) h[threadIdx.x] = 0;
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        const int2 p = sites[i];
+        if (!(p.x <= 0 || p.x >= W || p.y <= 0 || p.y >= H)) {
+            const int cx = (int)((long long)p.x * G / W), cy = (int)((long long)p.y * G / H);
+            const int c = max(coarse[cy * G + cx], 1);
+            atomicAdd(&h[31 - __clz(c)], 1);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 32 && h[threadIdx.x]) atomicAdd(&hist[threadIdx.x], h[threadIdx.x]);
+}
+
+__global__ void k_pick_grid(const int *__restrict__ hist, int n, int W, int H, int G, int s_fixed,
+                            int s_min, int s_max, WsHeader *hdr) {
+    int s = s_fixed;
+    if (s <= 0) {
+        long long acc = 0;
+        int bin = 0;
+        for (int b = 0; b < 32; b++) {
+            acc += hist[b];
+            if (2 * acc >= n) { bin = b; break; }
+        }
+        const double cmed = 1.4142135623730951 * (double)(1ll << bin);
+        const double area = ((double)W / G) * ((double)H / G);
+        s = (int)sqrt(2.0 * area / cmed);
+        s = max(s_min, min(s_max, s));
+    }
+    s = max(s, 1);
+    hdr->s = s;
+    hdr->m1 = (W + s - 1) / s;
+    hdr->m2 = (H + s - 1) / s;
+    hdr->m = hdr->m1 * hdr->m2;
+}
+
+__global__ void k_bucket_count(const int2 *__restrict__ sites, int n, int W, int H,
                                int *__restrict__ bcount, int *__restrict__ rank, WsHeader *hdr) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -36,18 +90,20 @@ __global__ void k_bucket_count(const int2 *__restrict__ sites, int n, int W, int
         rank[i] = -1;
         return;
     }
-    const int b = (p.y / s) * m1 + p.x / s;
+    const int s = hdr->s;
+    const int b = (p.y / s) * hdr->m1 + p.x / s;
     rank[i] = atomicAdd(&bcount[b], 1);
 }
 
-__global__ void k_bucket_scatter(const int2 *__restrict__ sites, int n, int s, int m1,
+__global__ void k_bucket_scatter(const int2 *__restrict__ sites, int n,
                                  const int *__restrict__ bstart, const int *__restrict__ rank,
                                  int2 *__restrict__ sxy, int *__restrict__ sid, const WsHeader *hdr) {
     if (hdr->err) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int2 p = sites[i];
-    const int b = (p.y / s) * m1 + p.x / s;
+    const int s = hdr->s;
+    const int b = (p.y / s) * hdr->m1 + p.x / s;
     const int pos = bstart[b] + rank[i];
     sxy[pos] = p;
     sid[pos] = i;
@@ -55,13 +111,14 @@ __global__ void k_bucket_scatter(const int2 *__restrict__ sites, int n, int s, i
 
 // Distinct sites (Section 2): equal sites fall into the same bucket, so a
 // comparison inside each bucket finds every duplicate.
-__global__ void k_dup_check(const int2 *__restrict__ sxy, int n, int s, int m1,
-                            const int *__restrict__ bstart, WsHeader *hdr) {
+__global__ void k_dup_check(const int2 *__restrict__ sxy, int n, const int *__restrict__ bstart,
+                            WsHeader *hdr) {
     if (hdr->err) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int2 p = sxy[i];
-    const int b = (p.y / s) * m1 + p.x / s;
+    const int s = hdr->s;
+    const int b = (p.y / s) * hdr->m1 + p.x / s;
     const int a = bstart[b], e = bstart[b + 1];
     for (int j = a; j < e; j++) {
         if (j == i) continue;
@@ -104,10 +161,11 @@ __device__ T block_exclusive(T v, T *sh, T &total) {
 }
 
 template <class T>
-__global__ void k_scan_reduce(const int *__restrict__ in, int n, T *__restrict__ partial,
-                              const WsHeader *hdr) {
+__global__ void k_scan_reduce(const int *__restrict__ in, int n, const int *n_dev,
+                              T *__restrict__ partial, const WsHeader *hdr) {
     __shared__ T sh[32];
     if (hdr->err) return;
+    if (n_dev) n = min(n, *n_dev);
     const int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_I;
     T s = 0;
 #pragma unroll
@@ -134,10 +192,12 @@ __global__ void k_scan_partials(T *__restrict__ partial, int nb, const WsHeader 
 
 // out[i] = sum of in[0..i) for i < n, and out[n] = total; optionally *tot = total.
 template <class T>
-__global__ void k_scan_down(const int *__restrict__ in, int n, const T *__restrict__ partial,
-                            T *__restrict__ out, long long *tot, const WsHeader *hdr) {
+__global__ void k_scan_down(const int *__restrict__ in, int n, const int *n_dev,
+                            const T *__restrict__ partial, T *__restrict__ out, long long *tot,
+                            const WsHeader *hdr) {
     __shared__ T sh[32];
     if (hdr->err) return;
+    if (n_dev) n = min(n, *n_dev);
     const int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_I;
     T v[SCAN_I];
     T s = 0;
@@ -160,14 +220,15 @@ __global__ void k_scan_down(const int *__restrict__ in, int n, const T *__restri
     }
 }
 
+// Exclusive scan of in[0..n) (n = min(n_max, *n_dev) when n_dev is given).
 template <class T>
-static void scan(const int *in, int n, T *out, T *partial, long long *tot, WsHeader *hdr,
-                 cudaStream_t st) {
-    const int nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+static void scan(const int *in, int n_max, const int *n_dev, T *out, T *partial, long long *tot,
+                 WsHeader *hdr, cudaStream_t st) {
+    const int nb = (n_max + SCAN_TILE - 1) / SCAN_TILE;
     const int nbb = nb > 0 ? nb : 1;
-    k_scan_reduce<T><<<nbb, SCAN_T, 0, st>>>(in, n, partial, hdr);
+    k_scan_reduce<T><<<nbb, SCAN_T, 0, st>>>(in, n_max, n_dev, partial, hdr);
     k_scan_partials<T><<<1, SCAN_T, 0, st>>>(partial, nbb, hdr);
-    k_scan_down<T><<<nbb, SCAN_T, 0, st>>>(in, n, partial, out, tot, hdr);
+    k_scan_down<T><<<nbb, SCAN_T, 0, st>>>(in, n_max, n_dev, partial, out, tot, hdr);
 }
 
 // ---------------------------------------------------------------------------
@@ -259,9 +320,9 @@ __global__ void k_compact(CompactParams Q) {
 // ---------------------------------------------------------------------------
 
 struct Layout {
-    int s, m1, m2, lanes, target;
+    int s_fixed, s_min, s_max, m_max, G, lanes, target;
     size_t hdr, bstart, rank, sxy, sid, partial, ecount, dcount, loc, del_ptr, slot, spill,
-        deferred, deferred2, gcount, grho2, gpos, total;
+        deferred, deferred2, gcount, grho2, gpos, coarse, total;
     int spill_cap;
     int n_partial;
 };
@@ -282,25 +343,36 @@ static bool resolve(int64_t n, vor_box box, const vor_opts *o, Layout &L) {
     vor_opts d;
     vor_opts_default(&d);
     if (!o) o = &d;
-    // bucket side: about 2 sites per bucket on average for uniform sites
+    // bucket side: chosen on the device from the site density (k_pick_grid),
+    // between s_min (at most max(4n, 4096) buckets) and s_max (a quarter of
+    // the average density); or fixed by the caller
+    const long long area = (long long)box.w * box.h;
+    const long long mcap = n * 4 > 4096 ? n * 4 : 4096;
+    L.s_min = (int)isqrt_floor(area / mcap);
+    while ((long long)L.s_min * L.s_min * mcap < area) L.s_min++;
+    L.s_max = (int)isqrt_floor(8 * area / n);
+    if (L.s_max < L.s_min) L.s_max = L.s_min;
+    if (L.s_max > (1 << 20)) L.s_max = 1 << 20;
+    L.s_fixed = 0;
     if (o->bucket_side > 0) {
         if (o->bucket_side > (1 << 20)) return false;
-        L.s = o->bucket_side;
-    } else {
-        const long long area = (long long)box.w * box.h;
-        long long side = isqrt_floor(2 * area / n);
-        if (side < 1) side = 1;
-        if (side > (1 << 20)) side = 1 << 20;
-        L.s = (int)side;
+        L.s_fixed = o->bucket_side;
     }
-    L.m1 = (box.w + L.s - 1) / L.s;
-    L.m2 = (box.h + L.s - 1) / L.s;
-    if ((long long)L.m1 * L.m2 > (1ll << 28)) return false;
+    {
+        const int smallest = L.s_fixed > 0 ? L.s_fixed : L.s_min;
+        const long long m1 = (box.w + smallest - 1) / smallest, m2 = (box.h + smallest - 1) / smallest;
+        if (m1 * m2 > (1ll << 28)) return false;
+        L.m_max = (int)(m1 * m2);
+    }
+    {
+        long long g = isqrt_floor(n) / 8;
+        L.G = (int)(g < 16 ? 16 : (g > 1024 ? 1024 : g));
+    }
     L.lanes = o->lanes_per_cell > 0 ? o->lanes_per_cell : 1;
     if (L.lanes != 1 && L.lanes != 2 && L.lanes != 4 && L.lanes != 8 && L.lanes != 16 && L.lanes != 32) return false;
     L.target = o->target > 0 ? o->target : 22;
     if (L.target > 40) return false;
-    const size_t m = (size_t)L.m1 * L.m2;
+    const size_t m = (size_t)L.m_max;
     const size_t nn = (size_t)n;
     const int nb_b = (int)((m + SCAN_TILE - 1) / SCAN_TILE), nb_n = (int)((nn + SCAN_TILE - 1) / SCAN_TILE);
     L.n_partial = (nb_b > nb_n ? nb_b : nb_n) + 1;
@@ -323,6 +395,7 @@ static bool resolve(int64_t n, vor_box box, const vor_opts *o, Layout &L) {
     L.gcount = at;   at = align256(at + nn * 4);
     L.grho2 = at;    at = align256(at + nn * 8);
     L.gpos = at;     at = align256(at + nn * 4 * (size_t)first_pass_gather_width());
+    L.coarse = at;   at = align256(at + (size_t)L.G * L.G * 4 + 32 * 4);
     L.total = at;
     return true;
 }
@@ -359,24 +432,31 @@ static int launch_build(const vor_site *d_sites, int64_t n64, vor_box box, const
     int *deferred = (int *)(base + L.deferred);
     int *deferred2 = (int *)(base + L.deferred2);
     const int2 *sites = (const int2 *)d_sites;
-    const int m = L.m1 * L.m2;
+    const int m = L.m_max;
 
     mark(0, st);
     if (cudaMemsetAsync(hdr, 0, 256, st) != cudaSuccess) return VOR_E_CUDA;
     if (cudaMemsetAsync(bstart, 0, (size_t)(m + 1) * 4, st) != cudaSuccess) return VOR_E_CUDA;
     const int T = 256;
     const int gn = (n + T - 1) / T;
-    k_bucket_count<<<gn, T, 0, st>>>(sites, n, box.w, box.h, L.s, L.m1, bstart, rank, hdr);
-    scan<int>(bstart, m, bstart, (int *)partial, nullptr, hdr, st);
-    k_bucket_scatter<<<gn, T, 0, st>>>(sites, n, L.s, L.m1, bstart, rank, sxy, sid, hdr);
-    if (o->check_duplicates) k_dup_check<<<gn, T, 0, st>>>(sxy, n, L.s, L.m1, bstart, hdr);
+    int *coarse = (int *)(base + L.coarse), *hist = coarse + (size_t)L.G * L.G;
+    if (L.s_fixed <= 0) {
+        if (cudaMemsetAsync(coarse, 0, ((size_t)L.G * L.G + 32) * 4, st) != cudaSuccess) return VOR_E_CUDA;
+        k_probe_count<<<gn, T, 0, st>>>(sites, n, box.w, box.h, L.G, coarse);
+        k_probe_hist<<<gn, T, 0, st>>>(sites, n, box.w, box.h, L.G, coarse, hist);
+    }
+    k_pick_grid<<<1, 1, 0, st>>>(hist, n, box.w, box.h, L.G, L.s_fixed, L.s_min, L.s_max, hdr);
+    k_bucket_count<<<gn, T, 0, st>>>(sites, n, box.w, box.h, bstart, rank, hdr);
+    scan<int>(bstart, m, &hdr->m, bstart, (int *)partial, nullptr, hdr, st);
+    k_bucket_scatter<<<gn, T, 0, st>>>(sites, n, bstart, rank, sxy, sid, hdr);
+    if (o->check_duplicates) k_dup_check<<<gn, T, 0, st>>>(sxy, n, bstart, hdr);
     if (cudaGetLastError() != cudaSuccess) return VOR_E_CUDA;
     mark(1, st);
 
     CellParams P;
     memset(&P, 0, sizeof(P));
     P.sites = sites; P.sxy = sxy; P.sid = sid; P.bstart = bstart;
-    P.n = n; P.W = box.w; P.H = box.h; P.s = L.s; P.m1 = L.m1; P.m2 = L.m2;
+    P.n = n; P.W = box.w; P.H = box.h;
     P.target = L.target; P.exact_only = o->exact_only; P.collect_stats = o->collect_stats;
     P.ecount = ecount; P.dcount = dcount; P.loc = loc; P.slot = slot; P.spill = spill;
     P.spill_cap = L.spill_cap;
@@ -414,8 +494,9 @@ static int launch_build(const vor_site *d_sites, int64_t n64, vor_box box, const
     if (launch_cells_large(PL, n, st) != cudaSuccess) return VOR_E_CUDA;
     mark(3, st);
 
-    scan<long long>(ecount, n, (long long *)out->cell_ptr, partial, (long long *)out->totals, hdr, st);
-    scan<long long>(dcount, n, del_ptr, partial, (long long *)out->totals + 1, hdr, st);
+    scan<long long>(ecount, n, nullptr, (long long *)out->cell_ptr, partial, (long long *)out->totals,
+                    hdr, st);
+    scan<long long>(dcount, n, nullptr, del_ptr, partial, (long long *)out->totals + 1, hdr, st);
     CompactParams Q;
     Q.sites = sites; Q.n = n; Q.W = box.w; Q.H = box.h;
     Q.ecount = ecount; Q.dcount = dcount; Q.loc = loc; Q.slot = slot; Q.spill = spill;
