@@ -57,6 +57,7 @@ extern "C" {
 #define VOR_E_CAPACITY (-6)      /* a cell exceeded the large-cell capacities */
 #define VOR_E_CUDA (-7)          /* a CUDA runtime call failed               */
 #define VOR_E_INTERNAL (-8)      /* an internal consistency check failed     */
+#define VOR_E_SCRATCH_LIMIT (-9) /* vor_build_noalloc: n needs more than its static scratch */
 
 #define VOR_SIDE_BOTTOM (-1)
 #define VOR_SIDE_RIGHT (-2)
@@ -176,6 +177,38 @@ int vor_build_host(const vor_site *h_sites, int64_t n, vor_box box, const vor_op
  * at a time. */
 int vor_stage_timing(int enable);
 int vor_stage_ms(float *ms, int max_stages);
+
+/* Build without allocating any device memory.
+ *
+ * The paper has no counterpart of this entry point; it serves callers that
+ * cannot allocate device memory when they need a diagram, such as a plug-in
+ * inside a host application whose framework owns the whole device memory
+ * pool, or a real-time deployment that forbids device allocation after
+ * start-up.
+ *
+ * The caller provides the sites (d_sites, as for vor_build_async) and the
+ * output buffers (out, as for vor_build_async).  The workspace is a static
+ * device array of VOR_NOALLOC_SCRATCH_BYTES (64 MiB) inside the library; it
+ * occupies that memory on every GPU where it has been loaded until the
+ * process exits.  n must satisfy vor_workspace_bytes(n, box, opts) <=
+ * VOR_NOALLOC_SCRATCH_BYTES (up to 199,672 sites in a 2^20 x 2^20 box with the
+ * default options); larger n is rejected with VOR_E_SCRATCH_LIMIT before any
+ * work is launched.  No cudaMalloc, cudaFree or other allocating routine is called.
+ *
+ * The first call on a device looks up the array's device address with
+ * cudaGetSymbolAddress (with that device current) and caches it; make that
+ * first call before any stream capture.  Every call shares the one array,
+ * and the build clears on the stream what must start at zero, so calls that
+ * overlap on the GPU (on different streams or from different threads) race
+ * and corrupt each other: serialise them.
+ *
+ * Synchronous: launches the build on the stream, waits for the stream and
+ * returns VOR_OK or the first error, including the errors vor_build_async
+ * leaves to vor_status (VOR_E_SITE_OUTSIDE, VOR_E_DUPLICATE,
+ * VOR_E_CAPACITY).  out->totals receives the totals. */
+#define VOR_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
+int vor_build_noalloc(const vor_site *d_sites, int64_t n, vor_box box, const vor_opts *opts,
+                      const vor_out *out, void *stream);
 
 /* Human-readable text of a VOR_* code. */
 const char *vor_strerror(int code);

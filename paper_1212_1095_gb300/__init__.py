@@ -21,14 +21,16 @@ from ._build import build_library
 __all__ = ["VorOpts", "VorStats", "VorOut", "VorError", "build_library", "library",
            "vor_opts_default", "vor_workspace_bytes", "vor_build_async", "vor_status",
            "vor_edge_capacity", "vor_delaunay_capacity", "vor_host_scratch_bytes",
-           "vor_build_host", "vor_strerror", "vor_stage_timing", "vor_stage_ms", "build", "build_host", "Diagram",
+           "vor_build_host", "vor_build_noalloc", "vor_strerror", "vor_stage_timing",
+           "vor_stage_ms", "build", "build_host", "Diagram",
            "SIDE_BOTTOM", "SIDE_RIGHT", "SIDE_TOP", "SIDE_LEFT"]
 
 SIDE_BOTTOM, SIDE_RIGHT, SIDE_TOP, SIDE_LEFT = -1, -2, -3, -4
 
 ERROR_NAMES = {0: "VOR_OK", -1: "VOR_E_INVALID_ARG", -2: "VOR_E_SITE_OUTSIDE",
                -3: "VOR_E_DUPLICATE", -4: "VOR_E_BOX_TOO_LARGE", -5: "VOR_E_OOM",
-               -6: "VOR_E_CAPACITY", -7: "VOR_E_CUDA", -8: "VOR_E_INTERNAL"}
+               -6: "VOR_E_CAPACITY", -7: "VOR_E_CUDA", -8: "VOR_E_INTERNAL",
+               -9: "VOR_E_SCRATCH_LIMIT"}
 
 
 class VorError(RuntimeError):
@@ -102,6 +104,8 @@ def library():
     lib.vor_stage_timing.restype = i32
     lib.vor_stage_ms.argtypes = [P, i32]
     lib.vor_stage_ms.restype = i32
+    lib.vor_build_noalloc.argtypes = [P, i64, VorBox, P, P, P]
+    lib.vor_build_noalloc.restype = i32
     lib.vor_strerror.argtypes = [i32]
     lib.vor_strerror.restype = ctypes.c_char_p
     _lib = lib
@@ -178,6 +182,14 @@ def vor_stage_ms() -> list[float]:
     if k < 0:
         raise VorError(k, "vor_stage_ms")
     return [float(buf[i]) for i in range(k)]
+
+
+def vor_build_noalloc(d_sites_ptr: int, n: int, box, opts: VorOpts, out: VorOut,
+                      stream: int) -> int:
+    """The allocation-free build (see include/vor.h): synchronous, returns the status."""
+    return int(library().vor_build_noalloc(ctypes.c_void_p(d_sites_ptr), int(n), _box(box),
+                                           ctypes.byref(opts), ctypes.byref(out),
+                                           ctypes.c_void_p(stream)))
 
 
 def vor_build_host(*args) -> int:

@@ -716,6 +716,7 @@ const char *vor_strerror(int code) {
     case VOR_E_CAPACITY: return "a cell exceeded the large-cell capacity";
     case VOR_E_CUDA: return "CUDA runtime error";
     case VOR_E_INTERNAL: return "internal consistency check failed";
+    case VOR_E_SCRATCH_LIMIT: return "n needs more workspace than the static scratch of vor_build_noalloc";
     default: return "unknown error";
     }
 }
