@@ -35,7 +35,7 @@ METRIC = "cells/s at n=1M uniform; batched sets/s and p50/p99 latency vs plain"
 BOX = 1 << 20
 WORKLOADS = {"uniform_1m": 1 << 20, "gauss_4m": 1 << 22}
 KERNEL_LAUNCHES_PER_STEP = 17   # our kernels per build (see vor_lib.cu pipeline)
-OPS_PER_EVAL = 8                # FP32/ALU operations of one filter evaluation
+OPS_PER_EVAL = 8                # FP32/ALU operations of one filter evaluation of a candidate
 
 
 def parse():
