@@ -26,7 +26,10 @@ cudaError_t launch_cells_large(const CellParams &P, int max_cells, cudaStream_t 
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int grid = sms * 2;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32, smem);
+    if (per_sm < 1) per_sm = 1;
+    int grid = sms * per_sm;
     if (max_cells < grid) grid = max_cells > 0 ? max_cells : 1;
     kern<<<grid, 32, smem, st>>>(P);
     return cudaGetLastError();

@@ -52,6 +52,7 @@ struct __align__(16) GroupSmem {
     short scw[SMAX], sccw[SMAX]; // their clockwise / counter-clockwise lines
     short emit[EMAX];            // edges, counter-clockwise
     float vx[EMAX], vy[EMAX];    // approximate vertices relative to p
+    short vord[EMAX];            // vertices by distance from p (large-cell certificate)
     int ncand;                   // candidate count while appending
     int flag;
 };
@@ -427,6 +428,153 @@ __device__ float polygon_vertices(GroupSmem<CMAX, SMAX, EMAX> &S, const int e, c
     return group_max<G>(R2, gmask);
 }
 
+
+// Site a (n = a - p, c = |n|^2) lies strictly inside the disc of vertex q of
+// the polygon (centre v, through p), i.e. cuts the polygon at v:
+// |a - v| < |p - v|  <=>  2 <n, v - p> > c.  Float filter, exact on doubt.
+template <class SM>
+__device__ __forceinline__ bool cuts_vertex(const SM &S, int e, int q, int nx, int ny, i64 cc) {
+    const float fnx = (float)nx, fny = (float)ny, fc = (float)cc;
+    const float vx = S.vx[q], vy = S.vy[q];
+    const float f = 2.f * fmaf(fnx, vx, fny * vy) - fc;
+    const float mg = 0x1p-16f * (2.f * (fabsf(fnx * vx) + fabsf(fny * vy)) + fc);
+    if (f > mg) return true;
+    if (f < -mg) return false;
+    int n1x, n1y, n2x, n2y;
+    i64 c1, c2, Nx, Ny, D;
+    cand_int(S, S.emit[q], n1x, n1y, c1);
+    cand_int(S, S.emit[q + 1 < e ? q + 1 : 0], n2x, n2y, c2);
+    intersect(n1x, n1y, c1, n2x, n2y, c2, Nx, Ny, D);
+    const i128 lhs = 2 * dot128(nx, ny, Nx, Ny) * (i128)(D > 0 ? 1 : -1);
+    return lhs > (i128)cc * (D > 0 ? D : -D);
+}
+
+// Large-cell certificate.  A site that is not a candidate can cut the
+// polygon only if it lies strictly inside the empty disc of some vertex v
+// (centre v, through p): the part of the polygon beyond a's bisector holds a
+// vertex v of the polygon with |a - v| < |p - v|.  Each round
+//   1. drops the candidates that carry no edge (their half-planes contain
+//      the polygon and every later, smaller polygon),
+//   2. scans, nearest vertex first, the sites inside both a vertex disc and
+//      the disc of radius rho around p (through the bucket rows both meet),
+//   3. adds the cutters found (as many as the table holds) and reruns the
+//      projector; with no cutter, rho doubles until it reaches 2R, where
+//      every vertex disc lies inside it and the polygon is the cell.
+template <int G, int CMAX, int SMAX, int EMAX, int RMAX>
+__device__ int certify_by_vertex_discs(const CellParams &P, GroupSmem<CMAX, SMAX, EMAX> &S,
+                                       const int2 p, const int i, i64 rho2, int &C, int &e,
+                                       const int gl, const unsigned gmask, Counters &cnt) {
+    const int s = P.hdr->s, m1 = P.hdr->m1, m2 = P.hdr->m2;
+    const i64 cxf = max(p.x, P.W - p.x), cyf = max(p.y, P.H - p.y);
+    const i64 far2 = cxf * cxf + cyf * cyf;            // no site is farther than a corner
+    for (int round = 0; round < 4096; round++) {
+        const float R2 = polygon_vertices<G>(S, e, gl, gmask);
+        group_sync<G>(gmask);
+        if (S.flag == 2) return CELL_FAIL;
+        if (gl == 0) {
+            // 1. keep the edge lines only: entries in ascending old index,
+            //    then renumber the edge list
+            for (int q = 0; q < e; q++) S.vord[q] = S.emit[q];
+            for (int x = 1; x < e; x++) {
+                const short key = S.vord[x];
+                int y = x - 1;
+                while (y >= 0 && S.vord[y] > key) { S.vord[y + 1] = S.vord[y]; y--; }
+                S.vord[y + 1] = key;
+            }
+            for (int q = 0; q < e; q++) {
+                const int src = S.vord[q];
+                if (src != q) { S.cand[q] = S.cand[src]; S.lab[q] = S.lab[src]; }
+            }
+            for (int q = 0; q < e; q++) {
+                int j = 0;
+                while (S.vord[j] != S.emit[q]) j++;
+                S.emit[q] = (short)j;
+            }
+            // vertices by increasing distance from p
+            for (int q = 0; q < e; q++) S.vord[q] = (short)q;
+            for (int x = 1; x < e; x++) {
+                const short key = S.vord[x];
+                const float kd = S.vx[key] * S.vx[key] + S.vy[key] * S.vy[key];
+                int y = x - 1;
+                while (y >= 0 && S.vx[S.vord[y]] * S.vx[S.vord[y]] + S.vy[S.vord[y]] * S.vy[S.vord[y]] > kd) {
+                    S.vord[y + 1] = S.vord[y];
+                    y--;
+                }
+                S.vord[y + 1] = key;
+            }
+            S.ncand = e;
+            S.flag = 0;
+        }
+        C = e;
+        group_sync<G>(gmask);
+        // 2. sites inside a vertex disc and within rho of p
+        const float rho = sqrtf((float)rho2) + 1.f;
+        for (int qi = 0; qi < e; qi++) {
+            const int q = S.vord[qi];
+            const float vx = (float)p.x + S.vx[q], vy = (float)p.y + S.vy[q];
+            const float r = sqrtf(S.vx[q] * S.vx[q] + S.vy[q] * S.vy[q]) * (1.f + 0x1p-10f) + 2.f;
+            const float ylo_all = fmaxf(vy - r, (float)p.y - rho), yhi_all = fminf(vy + r, (float)p.y + rho);
+            if (ylo_all > yhi_all) continue;
+            const int by0 = max(0, (int)floorf(ylo_all / (float)s));
+            const int by1 = min(m2 - 1, (int)floorf(yhi_all / (float)s));
+            for (int row = by0; row <= by1; row++) {
+                const float ylo = (float)row * (float)s, yhi = ylo + (float)s;
+                const float dv = fmaxf(0.f, fmaxf(ylo - vy, vy - yhi));
+                const float dp = fmaxf(0.f, fmaxf(ylo - (float)p.y, (float)p.y - yhi));
+                if (dv > r || dp > rho) continue;
+                const float hv = sqrtf(fmaxf(r * r - dv * dv, 0.f)) + 1.f;
+                const float hp = sqrtf(fmaxf(rho * rho - dp * dp, 0.f)) + 1.f;
+                const float xlo = fmaxf(vx - hv, (float)p.x - hp), xhi = fminf(vx + hv, (float)p.x + hp);
+                if (xlo > xhi) continue;
+                const int bx0 = max(0, (int)floorf(xlo / (float)s));
+                const int bx1 = min(m1 - 1, (int)floorf(xhi / (float)s));
+                if (bx0 > bx1) continue;
+                const int a = P.bstart[row * m1 + bx0], b = P.bstart[row * m1 + bx1 + 1];
+                for (int pos = a + gl; pos < b; pos += G) {
+                    if (pos == i) continue;
+                    const int2 site = P.sxy[pos];
+                    const int nx = site.x - p.x, ny = site.y - p.y;
+                    const i64 cc = (i64)nx * nx + (i64)ny * ny;
+                    if (cc > rho2) continue;
+                    cnt.annulus++;
+                    if (!cuts_vertex(S, e, q, nx, ny, cc)) continue;
+                    bool earlier = false;                  // found with a nearer vertex
+                    for (int qj = 0; qj < qi && !earlier; qj++)
+                        earlier = cuts_vertex(S, e, S.vord[qj], nx, ny, cc);
+                    if (earlier) continue;
+                    const int at = atomicAdd(&S.ncand, 1);
+                    if (at < CMAX) {
+                        const float fc = (float)cc, rc = 1.f / fc;
+                        S.cand[at] = make_float4((float)nx, (float)ny, rc, (float)(abs(nx) + abs(ny)) * rc);
+                        S.lab[at] = P.sid[pos];
+                    } else {
+                        S.flag = 1;
+                    }
+                }
+            }
+            group_sync<G>(gmask);
+            if (S.flag) break;                             // table full: use these first
+        }
+        group_sync<G>(gmask);
+        const int ncut = min(S.ncand, CMAX) - e;
+        if (ncut == 0) {
+            // 3. no cutter within rho: certified once rho covers 2R
+            const i64 need = (i64)(4.f * (R2 * (1.f + 0x1p-12f) + 1.f)) + 1;
+            if (need <= rho2 || rho2 >= far2) return CELL_OK;
+            cnt.widen++;
+            rho2 = min(min(need, rho2 < ((i64)1 << 60) / 4 ? 4 * rho2 + 4 : rho2), far2);
+            continue;
+        }
+        cnt.reruns++;
+        cnt.cands += ncut;
+        C = e + ncut;
+        e = projector<G, CMAX, SMAX, EMAX, RMAX>(S, C, gl, gmask, P.exact_only, cnt);
+        if (e < 0) return CELL_DEFER;
+        if (e < 3) return CELL_FAIL;
+    }
+    return CELL_FAIL;
+}
+
 // Work limits of a pass: the first pass defers cells that need more.
 template <bool LARGE>
 struct Limits {
@@ -491,9 +639,14 @@ __device__ int process_cell(const CellParams &P, GroupSmem<CMAX, SMAX, EMAX> &S,
     if (e < 3) return CELL_FAIL;
 
     // ---- 3. security-radius certificate -------------------------------------
+    if (LARGE) {
+        const int rc = certify_by_vertex_discs<G, CMAX, SMAX, EMAX, RMAX>(P, S, p, i, rho2, C, e, gl,
+                                                                          gmask, cnt);
+        if (rc != CELL_OK) return rc;
+    }
     // every site a with |a - p|^2 > rho2 has not been looked at and is
     // farther than rho
-    for (int iter = 0;; iter++) {
+    for (int iter = 0; !LARGE; iter++) {
         const float R2 = polygon_vertices<G>(S, e, gl, gmask);
         group_sync<G>(gmask);
         if (S.flag == 2) return CELL_FAIL;
@@ -620,7 +773,7 @@ __global__ void cells_kernel(CellParams P) {
 // first pass: 16 groups per block, small capacities, bounded certificate work
 constexpr int F_CMAX = 48, F_SMAX = 20, F_EMAX = 40, F_RMAX = 40, F_GROUPS = 16;
 // large-cell pass: one warp per cell, one cell per block
-constexpr int L_CMAX = 4096, L_SMAX = 512, L_EMAX = 1024, L_RMAX = 2048;
+constexpr int L_CMAX = 1024, L_SMAX = 256, L_EMAX = 256, L_RMAX = 1024;
 
 using FastSmem = GroupSmem<F_CMAX, F_SMAX, F_EMAX>;
 using LargeSmem = GroupSmem<L_CMAX, L_SMAX, L_EMAX>;

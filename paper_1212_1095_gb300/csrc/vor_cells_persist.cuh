@@ -21,20 +21,29 @@
 
 namespace vor {
 
-constexpr int P_NT = 64, P_CMAX = 44, P_SMAX = 16, P_EMAX = 32, P_RMAX = 32;
-constexpr int P_GMAX = P_CMAX - 4;   // sites per gathered list
+constexpr int P_NT = 64, P_SMAX = 16, P_EMAX = 32, P_RMAX = 32;
 constexpr int P_REFILL = 8;          // idle lanes that trigger a batched refill
+// first pass: 4 sides + up to 40 sites; second pass (the cells the first
+// disc did not certify): a disc with about 2.2 times the sites, 4 + 72 entries
+constexpr int P1_CMAX = 44, P2_CMAX = 76;
 
 struct GatherOut {
-    int *count;        // sites in the disc per sorted position (-1: more than P_GMAX)
-    long long *rho2;   // squared disc radius per sorted position
-    int *pos;          // P_GMAX sorted positions per cell
+    int *count;        // sites in the disc per cell (-1: more than gmax, or t >= cap)
+    long long *rho2;   // squared disc radius per cell
+    int *pos;          // gmax sorted positions per cell
+    int gmax;
+    int cap;           // cells the position buffer holds (later cells go to the next pass)
 };
 
-__global__ void __launch_bounds__(256) gather_kernel(CellParams P, GatherOut G) {
+// One thread per cell: the cells are the sorted positions t < P.n, or
+// P.cell_list[t] for t < *P.list_count; outputs are indexed by t.
+__global__ void __launch_bounds__(256) gather_kernel(CellParams P, GatherOut G, float target) {
     if (P.hdr->err) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= P.n) return;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int total = P.cell_list ? *P.list_count : P.n;
+    if (t >= total) return;
+    if (t >= G.cap) { G.count[t] = -1; return; }
+    const int i = P.cell_list ? P.cell_list[t] : t;
     const int2 p = P.sxy[i];
     const int s = P.hdr->s;
     const int bx = p.x / s, by = p.y / s;
@@ -47,13 +56,13 @@ __global__ void __launch_bounds__(256) gather_kernel(CellParams P, GatherOut G) 
         }
     }
     const float area = (float)nb9 * (float)s * (float)s;
-    i64 rho2 = (i64)((float)P.target * area / (3.14159265f * (float)max(c9 - 1, 1)));
+    i64 rho2 = (i64)(target * area / (3.14159265f * (float)max(c9 - 1, 1)));
     rho2 = max(min(rho2, (i64)(16.f * (float)s * (float)s)), (i64)4);
     const int r = (int)ceilf(sqrtf((float)rho2)) + 1;
     const int bx0 = p.x - r <= 0 ? 0 : (p.x - r) / s, bx1 = min(P.hdr->m1 - 1, (p.x + r) / s);
     const int by0 = p.y - r <= 0 ? 0 : (p.y - r) / s, by1 = min(P.hdr->m2 - 1, (p.y + r) / s);
     int cnt = 0;
-    int *dst = G.pos + (size_t)i * P_GMAX;
+    int *dst = G.pos + (size_t)t * G.gmax;
     for (int row = by0; row <= by1; row++) {
         const int a = P.bstart[row * P.hdr->m1 + bx0], b = P.bstart[row * P.hdr->m1 + bx1 + 1];
         for (int pos = a; pos < b; pos++) {
@@ -61,12 +70,12 @@ __global__ void __launch_bounds__(256) gather_kernel(CellParams P, GatherOut G) 
             const int2 q = P.sxy[pos];
             const int nx = q.x - p.x, ny = q.y - p.y;
             if ((i64)nx * nx + (i64)ny * ny > rho2) continue;
-            if (cnt < P_GMAX) dst[cnt] = pos;
+            if (cnt < G.gmax) dst[cnt] = pos;
             cnt++;
         }
     }
-    G.count[i] = cnt > P_GMAX ? -1 : cnt;
-    G.rho2[i] = rho2;
+    G.count[t] = cnt > G.gmax ? -1 : cnt;
+    G.rho2[t] = rho2;
 }
 
 template <int NT, int CMAX, int SMAX, int EMAX, int RMAX>
@@ -82,6 +91,7 @@ __global__ void __launch_bounds__(NT) cells_persist_kernel(CellParams P, GatherO
     t1::Counters cnt{};
     const int stride = gridDim.x * NT;
     int t = blockIdx.x * NT + threadIdx.x;
+    const int total = P.cell_list ? *P.list_count : P.n;
 
     // state of the thread's current cell
     int i = -1, C = 0;
@@ -174,10 +184,11 @@ __global__ void __launch_bounds__(NT) cells_persist_kernel(CellParams P, GatherO
                     }
                 }
                 // load the next cell of this thread's sequence
-                while (t < P.n) {
-                    i = t;
+                while (t < total) {
+                    const int tt = t;
+                    i = P.cell_list ? P.cell_list[t] : t;
                     t += stride;
-                    const int nc = G.count[i];
+                    const int nc = G.count[tt];
                     if (nc < 0) {                                   // disc too crowded
                         if (P.deferred) {
                             const int q = atomicAdd(P.deferred_count, 1);
@@ -189,12 +200,12 @@ __global__ void __launch_bounds__(NT) cells_persist_kernel(CellParams P, GatherO
                         continue;
                     }
                     p = P.sxy[i];
-                    rho2 = G.rho2[i];
+                    rho2 = G.rho2[tt];
                     T.put(0, t1::cand_of(0, -p.y, true));
                     T.put(1, t1::cand_of(P.W - p.x, 0, true));
                     T.put(2, t1::cand_of(0, P.H - p.y, true));
                     T.put(3, t1::cand_of(-p.x, 0, true));
-                    const int *src = G.pos + (size_t)i * P_GMAX;
+                    const int *src = G.pos + (size_t)tt * G.gmax;
                     for (int q = 0; q < nc; q++) {
                         const int pos = src[q];
                         const int2 a = P.sxy[pos];

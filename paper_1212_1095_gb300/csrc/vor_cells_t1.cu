@@ -1,39 +1,16 @@
-// vor_cells_t1.cu -- launcher of the one-thread-per-cell projector kernel.
+// vor_cells_t1.cu -- launchers of the one-thread-per-cell projector passes.
 #include "vor_cells_persist.cuh"
 
 namespace vor {
 
-template <bool WIDEN>
-static cudaError_t launch_t(const CellParams &P, cudaStream_t st) {
-    auto kern = cells_thread_kernel<T_NT, T_CMAX, T_SMAX, T_EMAX, T_RMAX, WIDEN>;
-    const int smem = T_NT * T_CMAX * (int)sizeof(float4);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, T_NT, smem);
-    if (per_sm < 1) per_sm = 1;
-    long long want = ((long long)(P.cell_list ? P.n_list : P.n) + T_NT - 1) / T_NT;
-    long long grid = (long long)sms * per_sm;
-    if (want < grid) grid = want;
-    if (grid < 1) grid = 1;
-    kern<<<(unsigned)grid, T_NT, smem, st>>>(P);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_cells_thread(const CellParams &P, bool widen, cudaStream_t st) {
-    return widen ? launch_t<true>(P, st) : launch_t<false>(P, st);
-}
-
-cudaError_t launch_cells_first_pass(const CellParams &P, int *gcount, long long *grho2, int *gpos,
-                                    cudaStream_t st) {
-    GatherOut G{gcount, grho2, gpos};
-    gather_kernel<<<(P.n + 255) / 256, 256, 0, st>>>(P, G);
+template <int CMAX>
+static cudaError_t launch_pass(const CellParams &P, const GatherOut &G, float target, cudaStream_t st) {
+    const int total_max = P.cell_list ? P.n_list : P.n;
+    gather_kernel<<<(total_max + 255) / 256, 256, 0, st>>>(P, G, target);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    auto kern = cells_persist_kernel<P_NT, P_CMAX, P_SMAX, P_EMAX, P_RMAX>;
-    const int smem = P_NT * P_CMAX * (int)sizeof(float4);
+    auto kern = cells_persist_kernel<P_NT, CMAX, P_SMAX, P_EMAX, P_RMAX>;
+    const int smem = P_NT * CMAX * (int)sizeof(float4);
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
@@ -41,7 +18,7 @@ cudaError_t launch_cells_first_pass(const CellParams &P, int *gcount, long long 
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, P_NT, smem);
     if (per_sm < 1) per_sm = 1;
-    long long want = ((long long)P.n + P_NT - 1) / P_NT;
+    long long want = ((long long)total_max + P_NT - 1) / P_NT;
     long long grid = (long long)sms * per_sm;
     if (want < grid) grid = want;
     if (grid < 1) grid = 1;
@@ -49,6 +26,19 @@ cudaError_t launch_cells_first_pass(const CellParams &P, int *gcount, long long 
     return cudaGetLastError();
 }
 
-int first_pass_gather_width() { return P_GMAX; }
+cudaError_t launch_cells_pass(const CellParams &P, int pass, int *gcount, long long *grho2, int *gpos,
+                              cudaStream_t st) {
+    // both passes share one position buffer of n * (P1_CMAX - 4) entries; the
+    // second pass lists fewer cells (the deferred ones) with more sites each
+    const long long entries = (long long)P.n * (P1_CMAX - 4);
+    if (pass == 1) {
+        GatherOut G{gcount, grho2, gpos, P1_CMAX - 4, P.n};
+        return launch_pass<P1_CMAX>(P, G, (float)P.target, st);
+    }
+    GatherOut G{gcount, grho2, gpos, P2_CMAX - 4, (int)(entries / (P2_CMAX - 4))};
+    return launch_pass<P2_CMAX>(P, G, 2.2f * (float)P.target, st);
+}
+
+int pass_gather_width() { return P1_CMAX - 4; }
 
 }  // namespace vor

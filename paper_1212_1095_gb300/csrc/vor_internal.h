@@ -63,10 +63,10 @@ struct CellParams {
 
 // Launchers (vor_cells.cu)
 cudaError_t launch_cells_fast(const CellParams &P, int lanes, cudaStream_t st);
-cudaError_t launch_cells_thread(const CellParams &P, bool widen, cudaStream_t st);
-cudaError_t launch_cells_first_pass(const CellParams &P, int *gcount, long long *grho2, int *gpos,
-                                    cudaStream_t st);
-int first_pass_gather_width();
+// one thread per cell; pass 1 over all cells, pass 2 over the list P.cell_list
+cudaError_t launch_cells_pass(const CellParams &P, int pass, int *gcount, long long *grho2, int *gpos,
+                              cudaStream_t st);
+int pass_gather_width();
 cudaError_t launch_cells_large(const CellParams &P, int max_cells, cudaStream_t st);
 int cells_fast_max_smem();
 int cells_large_capacity();

@@ -26,10 +26,10 @@ namespace vor {
 // K1: bucketing
 // ---------------------------------------------------------------------------
 
-// Site density probe: the bucket side is chosen so that the bucket of the
-// median site (by its own neighbourhood) holds about two sites.  A coarse
-// G x G grid counts the sites; each site reads its coarse cell's count into a
-// log2 histogram; the median bin gives the local density.
+// Site density probe: the bucket side is chosen so that a bucket around a
+// typical site holds about two sites.  A coarse G x G grid counts the sites;
+// the typical neighbourhood count is the geometric mean, over the sites, of
+// the count of their own coarse cell.
 __global__ void k_probe_count(const int2 *__restrict__ sites, int n, int W, int H, int G,
                               int *__restrict__ coarse) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -40,35 +40,34 @@ __global__ void k_probe_count(const int2 *__restrict__ sites, int n, int W, int 
     atomicAdd(&coarse[cy * G + cx], 1);
 }
 
-__global__ void k_probe_hist(const int2 *__restrict__ sites, int n, int W, int H, int G,
-                             const int *__restrict__ coarse, int *__restrict__ hist) {
-    __shared__ int h[32];
-    if (threadIdx.x < 32) h[threadIdx.x] = 0;
-    __syncthreads();
+__global__ void k_probe_mean(const int2 *__restrict__ sites, int n, int W, int H, int G,
+                             const int *__restrict__ coarse, double *__restrict__ acc) {
+    __shared__ float sh[8];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    float v = 0.f;
     if (i < n) {
         const int2 p = sites[i];
         if (!(p.x <= 0 || p.x >= W || p.y <= 0 || p.y >= H)) {
             const int cx = (int)((long long)p.x * G / W), cy = (int)((long long)p.y * G / H);
-            const int c = max(coarse[cy * G + cx], 1);
-            atomicAdd(&h[31 - __clz(c)], 1);
+            v = log2f((float)max(coarse[cy * G + cx], 1));
         }
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
     __syncthreads();
-    if (threadIdx.x < 32 && h[threadIdx.x]) atomicAdd(&hist[threadIdx.x], h[threadIdx.x]);
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += sh[w];
+        atomicAdd(acc, (double)t);
+    }
 }
 
-__global__ void k_pick_grid(const int *__restrict__ hist, int n, int W, int H, int G, int s_fixed,
+__global__ void k_pick_grid(const double *__restrict__ acc, int n, int W, int H, int G, int s_fixed,
                             int s_min, int s_max, WsHeader *hdr) {
     int s = s_fixed;
     if (s <= 0) {
-        long long acc = 0;
-        int bin = 0;
-        for (int b = 0; b < 32; b++) {
-            acc += hist[b];
-            if (2 * acc >= n) { bin = b; break; }
-        }
-        const double cmed = 1.4142135623730951 * (double)(1ll << bin);
+        const double cmed = exp2(acc[0] / (double)n);    // typical sites per coarse cell
         const double area = ((double)W / G) * ((double)H / G);
         s = (int)sqrt(2.0 * area / cmed);
         s = max(s_min, min(s_max, s));
@@ -394,8 +393,8 @@ static bool resolve(int64_t n, vor_box box, const vor_opts *o, Layout &L) {
     L.deferred2 = at; at = align256(at + nn * 4);
     L.gcount = at;   at = align256(at + nn * 4);
     L.grho2 = at;    at = align256(at + nn * 8);
-    L.gpos = at;     at = align256(at + nn * 4 * (size_t)first_pass_gather_width());
-    L.coarse = at;   at = align256(at + (size_t)L.G * L.G * 4 + 32 * 4);
+    L.gpos = at;     at = align256(at + nn * 4 * (size_t)pass_gather_width());
+    L.coarse = at;   at = align256(at + align256((size_t)L.G * L.G * 4) + 256);
     L.total = at;
     return true;
 }
@@ -439,13 +438,15 @@ static int launch_build(const vor_site *d_sites, int64_t n64, vor_box box, const
     if (cudaMemsetAsync(bstart, 0, (size_t)(m + 1) * 4, st) != cudaSuccess) return VOR_E_CUDA;
     const int T = 256;
     const int gn = (n + T - 1) / T;
-    int *coarse = (int *)(base + L.coarse), *hist = coarse + (size_t)L.G * L.G;
+    int *coarse = (int *)(base + L.coarse);
+    double *acc = (double *)(base + L.coarse + align256((size_t)L.G * L.G * 4));
     if (L.s_fixed <= 0) {
-        if (cudaMemsetAsync(coarse, 0, ((size_t)L.G * L.G + 32) * 4, st) != cudaSuccess) return VOR_E_CUDA;
+        if (cudaMemsetAsync(coarse, 0, align256((size_t)L.G * L.G * 4) + 256, st) != cudaSuccess)
+            return VOR_E_CUDA;
         k_probe_count<<<gn, T, 0, st>>>(sites, n, box.w, box.h, L.G, coarse);
-        k_probe_hist<<<gn, T, 0, st>>>(sites, n, box.w, box.h, L.G, coarse, hist);
+        k_probe_mean<<<gn, T, 0, st>>>(sites, n, box.w, box.h, L.G, coarse, acc);
     }
-    k_pick_grid<<<1, 1, 0, st>>>(hist, n, box.w, box.h, L.G, L.s_fixed, L.s_min, L.s_max, hdr);
+    k_pick_grid<<<1, 1, 0, st>>>(acc, n, box.w, box.h, L.G, L.s_fixed, L.s_min, L.s_max, hdr);
     k_bucket_count<<<gn, T, 0, st>>>(sites, n, box.w, box.h, bstart, rank, hdr);
     scan<int>(bstart, m, &hdr->m, bstart, (int *)partial, nullptr, hdr, st);
     k_bucket_scatter<<<gn, T, 0, st>>>(sites, n, bstart, rank, sxy, sid, hdr);
@@ -463,21 +464,22 @@ static int launch_build(const vor_site *d_sites, int64_t n64, vor_box box, const
     P.cell_list = nullptr; P.list_count = nullptr; P.n_list = 0;
     P.hdr = hdr;
     if (L.lanes == 1) {
-        // first pass: one thread per cell, no certificate widening
+        int *gcount = (int *)(base + L.gcount), *gpos = (int *)(base + L.gpos);
+        long long *grho2 = (long long *)(base + L.grho2);
+        // first pass over all cells: the cells its disc does not certify
+        // (or that exceed its table) go on to the second pass
         P.deferred = deferred;
         P.deferred_count = &hdr->ndeferred;
-        if (launch_cells_first_pass(P, (int *)(base + L.gcount), (long long *)(base + L.grho2),
-                                    (int *)(base + L.gpos), st) != cudaSuccess)
-            return VOR_E_CUDA;
+        if (launch_cells_pass(P, 1, gcount, grho2, gpos, st) != cudaSuccess) return VOR_E_CUDA;
         mark(2, st);
-        // second pass over the cells the first disc did not certify
+        // second pass: a disc with about 2.2 times the sites
         CellParams P2 = P;
         P2.cell_list = deferred;
         P2.list_count = &hdr->ndeferred;
         P2.n_list = n;
         P2.deferred = deferred2;
         P2.deferred_count = &hdr->ndeferred2;
-        if (launch_cells_thread(P2, true, st) != cudaSuccess) return VOR_E_CUDA;
+        if (launch_cells_pass(P2, 2, gcount, grho2, gpos, st) != cudaSuccess) return VOR_E_CUDA;
     } else {
         P.deferred = deferred2;
         P.deferred_count = &hdr->ndeferred2;
