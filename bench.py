@@ -346,8 +346,9 @@ def run_ours(args):
                    "parallelism": f"replicas x{ws_n}" if ws_n > 1 else "1 GPU"},
         "stages_ms": {"bucketing": statistics.mean(x[0] for x in stage_acc),
                       "projector_first_pass": kms,
-                      "projector_later_passes": statistics.mean(x[2] for x in stage_acc),
-                      "compaction": statistics.mean(x[3] for x in stage_acc), "step": ms},
+                      "projector_second_pass": statistics.mean(x[2] for x in stage_acc),
+                      "projector_large_cells": statistics.mean(x[3] for x in stage_acc),
+                      "compaction": statistics.mean(x[4] for x in stage_acc), "step": ms},
         "stats": stats,
         "roofline": roofline,
         "clocks": clk,

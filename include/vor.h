@@ -146,7 +146,7 @@ int vor_build_async(const vor_site *d_sites, int64_t n, vor_box box, const vor_o
 int vor_status(const void *d_workspace, void *stream, vor_stats *stats);
 
 /* Synchronous convenience form: allocates workspace and worst-case output
- * with cudaMallocAsync on the stream, builds, waits, and returns the outputs
+ * with cudaMalloc, builds, waits, and returns the outputs
  * (owned by the caller, free with vor_free_result).  *n_edges and *n_del
  * receive the totals.  The pointers in *out are device pointers. */
 int vor_build(const vor_site *d_sites, int64_t n, vor_box box, const vor_opts *opts,
@@ -169,9 +169,10 @@ int vor_build_host(const vor_site *h_sites, int64_t n, vor_box box, const vor_op
 /* Stage timing, off by default.  When enabled, vor_build_async records a
  * CUDA event on its stream before and after each stage; vor_stage_ms then
  * waits for the last event and writes the device milliseconds of the last
- * timed build: ms[0] bucketing (validation, count, scan, scatter, duplicate
- * check), ms[1] the projector kernel, ms[2] the large-cell pass, ms[3]
- * compaction (two scans and the CSR/Delaunay kernel).  Returns the number
+ * timed build: ms[0] bucketing (density probe, validation, count, scan,
+ * scatter, duplicate check), ms[1] the first projector pass, ms[2] the second
+ * pass, ms[3] the large-cell pass, ms[4] compaction (two scans and the
+ * CSR/Delaunay kernel).  Returns the number
  * of values written (<= max_stages) or a negative VOR_E_* code.  One process
  * wide set of events on the current device: meant for benchmarking one build
  * at a time. */
@@ -209,6 +210,49 @@ int vor_stage_ms(float *ms, int max_stages);
 #define VOR_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
 int vor_build_noalloc(const vor_site *d_sites, int64_t n, vor_box box, const vor_opts *opts,
                       const vor_out *out, void *stream);
+
+/* ---- Batches: many independent point sets in one build -------------------
+ *
+ * The paper computes one diagram at a time; the cells of a diagram are
+ * independent (Theorem 8.1(c,d)), and so are the cells of different
+ * diagrams.  A batch runs S independent sets through one pass of the
+ * pipeline (one launch per stage for the whole batch), which is what makes
+ * thousands of small sets cheap: a set of a few hundred sites cannot fill
+ * the GPU on its own.
+ *
+ * Set j (0 <= j < S) is the sites d_sites[set_ptr[j] .. set_ptr[j+1]) in the
+ * box boxes[j]; set_ptr[0] = 0, set_ptr is non-decreasing (empty sets are
+ * allowed) and N = set_ptr[S] <= 2^27.  Each set follows the conventions of
+ * a single build in its own box, with labels LOCAL to the set: a cell of set
+ * j lists neighbour indices in [0, n_j) or sides, and its Delaunay pairs
+ * (k, l), k < l, are local indices too.
+ *
+ * Outputs are concatenated over the sets (same vor_out buffers):
+ *   cell_ptr int64[N + 1]: the cells of set j are cell_ptr[set_ptr[j] ..
+ *     set_ptr[j+1]] (offsets into the shared edge arrays);
+ *   edge_label, vx, vy: capacity >= vor_batch_edge_capacity(N, S);
+ *   del_edge: capacity >= vor_batch_delaunay_capacity(N, S) pairs, the pairs
+ *     of set j at del_edge[2 * d_del_set_ptr[j] .. 2 * d_del_set_ptr[j+1]);
+ *   d_del_set_ptr int64[S + 1] (device, caller-allocated): written.
+ *   totals: total edges and total Delaunay pairs of the batch.
+ *
+ * Both the host and the device copies of set_ptr and boxes are required:
+ * the host copies size the workspace and the launches, the device copies
+ * feed the kernels without a host-to-device copy (so the build can be
+ * captured into a CUDA graph).  They must hold the same values; a
+ * difference that the device detects is reported as VOR_E_INVALID_ARG by
+ * vor_status.  An error (a site outside its box, a duplicate inside a set,
+ * a capacity limit) fails the whole batch.  A single build is the batch of
+ * one set. */
+int64_t vor_batch_edge_capacity(int64_t n_total, int32_t n_sets);
+int64_t vor_batch_delaunay_capacity(int64_t n_total, int32_t n_sets);
+int64_t vor_batch_workspace_bytes(const int64_t *h_set_ptr, int32_t n_sets, const vor_box *h_boxes,
+                                  const vor_opts *opts);
+int vor_build_batch_async(const vor_site *d_sites, const int64_t *d_set_ptr,
+                          const int64_t *h_set_ptr, int32_t n_sets, const vor_box *d_boxes,
+                          const vor_box *h_boxes, const vor_opts *opts, void *d_workspace,
+                          int64_t ws_bytes, const vor_out *out, int64_t *d_del_set_ptr,
+                          void *stream);
 
 /* Human-readable text of a VOR_* code. */
 const char *vor_strerror(int code);

@@ -22,7 +22,9 @@ __all__ = ["VorOpts", "VorStats", "VorOut", "VorError", "build_library", "librar
            "vor_opts_default", "vor_workspace_bytes", "vor_build_async", "vor_status",
            "vor_edge_capacity", "vor_delaunay_capacity", "vor_host_scratch_bytes",
            "vor_build_host", "vor_build_noalloc", "vor_strerror", "vor_stage_timing",
-           "vor_stage_ms", "build", "build_host", "Diagram",
+           "vor_stage_ms", "build", "build_host", "Diagram", "vor_batch_edge_capacity",
+           "vor_batch_delaunay_capacity", "vor_batch_workspace_bytes", "vor_build_batch_async",
+           "BatchWorkspace", "BatchDiagram", "build_batch",
            "SIDE_BOTTOM", "SIDE_RIGHT", "SIDE_TOP", "SIDE_LEFT"]
 
 SIDE_BOTTOM, SIDE_RIGHT, SIDE_TOP, SIDE_LEFT = -1, -2, -3, -4
@@ -106,6 +108,14 @@ def library():
     lib.vor_stage_ms.restype = i32
     lib.vor_build_noalloc.argtypes = [P, i64, VorBox, P, P, P]
     lib.vor_build_noalloc.restype = i32
+    lib.vor_batch_edge_capacity.argtypes = [i64, ctypes.c_int32]
+    lib.vor_batch_edge_capacity.restype = i64
+    lib.vor_batch_delaunay_capacity.argtypes = [i64, ctypes.c_int32]
+    lib.vor_batch_delaunay_capacity.restype = i64
+    lib.vor_batch_workspace_bytes.argtypes = [P, ctypes.c_int32, P, P]
+    lib.vor_batch_workspace_bytes.restype = i64
+    lib.vor_build_batch_async.argtypes = [P, P, P, ctypes.c_int32, P, P, P, P, i64, P, P, P]
+    lib.vor_build_batch_async.restype = i32
     lib.vor_strerror.argtypes = [i32]
     lib.vor_strerror.restype = ctypes.c_char_p
     _lib = lib
@@ -176,9 +186,9 @@ def vor_stage_timing(enable: bool) -> int:
 
 
 def vor_stage_ms() -> list[float]:
-    """Device ms of [bucketing, projector, large cells, compaction] of the last build."""
-    buf = (ctypes.c_float * 4)()
-    k = int(library().vor_stage_ms(buf, 4))
+    """Device ms of [bucketing, pass 1, pass 2, large cells, compaction] of the last build."""
+    buf = (ctypes.c_float * 5)()
+    k = int(library().vor_stage_ms(buf, 5))
     if k < 0:
         raise VorError(k, "vor_stage_ms")
     return [float(buf[i]) for i in range(k)]
@@ -194,6 +204,34 @@ def vor_build_noalloc(d_sites_ptr: int, n: int, box, opts: VorOpts, out: VorOut,
 
 def vor_build_host(*args) -> int:
     return int(library().vor_build_host(*args))
+
+
+def vor_batch_edge_capacity(n_total: int, n_sets: int) -> int:
+    return int(library().vor_batch_edge_capacity(int(n_total), int(n_sets)))
+
+
+def vor_batch_delaunay_capacity(n_total: int, n_sets: int) -> int:
+    return int(library().vor_batch_delaunay_capacity(int(n_total), int(n_sets)))
+
+
+def vor_batch_workspace_bytes(set_ptr_np, boxes_np, opts: VorOpts | None = None) -> int:
+    """set_ptr_np: int64 [S+1] host array; boxes_np: int32 [S, 2] host array."""
+    import numpy as np
+    sp = np.ascontiguousarray(set_ptr_np, dtype=np.int64)
+    bx = np.ascontiguousarray(boxes_np, dtype=np.int32)
+    return int(library().vor_batch_workspace_bytes(
+        ctypes.c_void_p(sp.ctypes.data), int(sp.shape[0] - 1), ctypes.c_void_p(bx.ctypes.data),
+        ctypes.byref(opts) if opts is not None else None))
+
+
+def vor_build_batch_async(d_sites_ptr: int, d_set_ptr: int, set_ptr_np, d_boxes: int, boxes_np,
+                          opts: VorOpts, ws_ptr: int, ws_bytes: int, out: VorOut,
+                          d_del_set_ptr: int, stream: int) -> int:
+    P = ctypes.c_void_p
+    return int(library().vor_build_batch_async(
+        P(d_sites_ptr), P(d_set_ptr), P(set_ptr_np.ctypes.data), int(set_ptr_np.shape[0] - 1),
+        P(d_boxes), P(boxes_np.ctypes.data), ctypes.byref(opts), P(ws_ptr), int(ws_bytes),
+        ctypes.byref(out), P(d_del_set_ptr), P(stream)))
 
 
 # ------------------------------------------------------------ convenience ----
@@ -300,3 +338,99 @@ def build_host(sites_np, box, **opts):
     if rc != 0:
         raise VorError(rc, "vor_build_host")
     return Diagram(cell_ptr, labels[:ne.value], vx[:ne.value], vy[:ne.value], dl[:nd.value], {})
+
+
+@dataclass
+class BatchDiagram:
+    """Result of a batch build: concatenated arrays, labels local to each set."""
+    set_ptr: object       # int64 [S+1] (host)
+    cell_ptr: object      # int64 [N+1]
+    labels: object        # int32 [E]
+    vx: object
+    vy: object
+    delaunay: object      # int32 [M, 2]
+    del_set_ptr: object   # int64 [S+1]
+    stats: dict
+
+    def set(self, j: int) -> Diagram:
+        """The diagram of set j (views; cell_ptr rebased to the set's first edge)."""
+        a, b = int(self.set_ptr[j]), int(self.set_ptr[j + 1])
+        cp = self.cell_ptr[a:b + 1]
+        e0, e1 = int(cp[0]), int(cp[-1])
+        d0, d1 = int(self.del_set_ptr[j]), int(self.del_set_ptr[j + 1])
+        return Diagram(cp - e0, self.labels[e0:e1], self.vx[e0:e1], self.vy[e0:e1],
+                       self.delaunay[d0:d1], {})
+
+
+class BatchWorkspace:
+    """Device buffers for repeated batch builds with fixed set offsets and boxes."""
+
+    def __init__(self, set_ptr, boxes, opts: VorOpts, device=None):
+        import numpy as np
+        import torch
+        self.set_ptr = np.ascontiguousarray(set_ptr, dtype=np.int64)
+        self.boxes = np.ascontiguousarray(boxes, dtype=np.int32).reshape(-1, 2)
+        self.n_sets = int(self.set_ptr.shape[0] - 1)
+        if self.boxes.shape[0] != self.n_sets:
+            raise ValueError("one box per set")
+        self.n = int(self.set_ptr[-1])
+        self.opts = opts
+        dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
+        nb = vor_batch_workspace_bytes(self.set_ptr, self.boxes, opts)
+        if nb < 0:
+            raise VorError(-1, "vor_batch_workspace_bytes")
+        self.ws = torch.empty(nb + 256, dtype=torch.uint8, device=dev)
+        self.ws_ptr = (self.ws.data_ptr() + 255) & ~255
+        self.ws_bytes = nb
+        self.d_set_ptr = torch.from_numpy(self.set_ptr).to(dev)
+        self.d_boxes = torch.from_numpy(self.boxes).to(dev)
+        ec = vor_batch_edge_capacity(self.n, self.n_sets)
+        dc = vor_batch_delaunay_capacity(self.n, self.n_sets)
+        self.cell_ptr = torch.empty(self.n + 1, dtype=torch.int64, device=dev)
+        self.labels = torch.empty(ec, dtype=torch.int32, device=dev)
+        self.vx = torch.empty(ec, dtype=torch.float64, device=dev)
+        self.vy = torch.empty(ec, dtype=torch.float64, device=dev)
+        self.del_edge = torch.empty((dc, 2), dtype=torch.int32, device=dev)
+        self.del_set_ptr = torch.zeros(self.n_sets + 1, dtype=torch.int64, device=dev)
+        self.totals = torch.zeros(2, dtype=torch.int64, device=dev)
+        self.out = VorOut(self.cell_ptr.data_ptr(), self.labels.data_ptr(), self.vx.data_ptr(),
+                          self.vy.data_ptr(), self.del_edge.data_ptr(), self.totals.data_ptr(),
+                          ec, dc)
+
+    def launch(self, d_sites, stream=None) -> None:
+        """Enqueue a build of the concatenated sites (int32 [N,2] on the device)."""
+        import torch
+        if d_sites.shape[0] != self.n:
+            raise ValueError("sites do not match the set offsets")
+        s = stream if stream is not None else torch.cuda.current_stream()
+        rc = vor_build_batch_async(d_sites.data_ptr(), self.d_set_ptr.data_ptr(), self.set_ptr,
+                                   self.d_boxes.data_ptr(), self.boxes, self.opts, self.ws_ptr,
+                                   self.ws_bytes, self.out, self.del_set_ptr.data_ptr(),
+                                   s.cuda_stream)
+        if rc != 0:
+            raise VorError(rc, "vor_build_batch_async")
+
+    def finish(self, stream=None) -> BatchDiagram:
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream()
+        rc, st = vor_status(self.ws_ptr, s.cuda_stream)
+        if rc != 0:
+            raise VorError(rc, "vor_status")
+        ne, nd = (int(v) for v in self.totals.cpu())
+        return BatchDiagram(self.set_ptr, self.cell_ptr, self.labels[:ne], self.vx[:ne],
+                            self.vy[:ne], self.del_edge[:nd], self.del_set_ptr, st.as_dict())
+
+
+def build_batch(sites, set_ptr, boxes, **opts) -> BatchDiagram:
+    """Diagrams of many independent sets in one build.
+
+    sites: torch int32 [N,2] on the GPU, the sets one after another;
+    set_ptr: int64 [S+1] host offsets; boxes: int32 [S,2] host (w, h) per set.
+    """
+    import torch
+    if not (hasattr(sites, "is_cuda") and sites.is_cuda):
+        raise TypeError("sites must be a CUDA tensor (int32 [N,2])")
+    sites = sites.to(torch.int32).contiguous()
+    ws = BatchWorkspace(set_ptr, boxes, vor_opts_default(**opts), device=sites.device)
+    ws.launch(sites)
+    return ws.finish()

@@ -21,15 +21,9 @@ cudaError_t launch_cells_fast(const CellParams &P, int lanes, cudaStream_t st) {
 cudaError_t launch_cells_large(const CellParams &P, int max_cells, cudaStream_t st) {
     auto kern = cells_kernel<32, L_CMAX, L_SMAX, L_EMAX, L_RMAX, true>;
     const int smem = (int)sizeof(LargeSmem);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    int grid = 0;
+    cudaError_t e = resident_grid((const void *)kern, 32, smem, grid);
     if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32, smem);
-    if (per_sm < 1) per_sm = 1;
-    int grid = sms * per_sm;
     if (max_cells < grid) grid = max_cells > 0 ? max_cells : 1;
     kern<<<grid, 32, smem, st>>>(P);
     return cudaGetLastError();

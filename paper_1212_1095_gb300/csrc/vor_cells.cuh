@@ -351,18 +351,18 @@ __device__ int projector(GroupSmem<CMAX, SMAX, EMAX> &S, const int C, const int 
 // when the table would grow past cap.  Returns the number of sites examined
 // (for the work budget).
 template <int G, int CMAX, int SMAX, int EMAX>
-__device__ int scan_disc(const CellParams &P, GroupSmem<CMAX, SMAX, EMAX> &S, const int2 p,
-                         const int self, const i64 r2lo, const i64 r2hi, const bool cut_only,
-                         const int e, const int cap, const int gl, Counters &cnt) {
-    const int s = P.hdr->s;
+__device__ int scan_disc(const CellParams &P, const CellGrid &g, GroupSmem<CMAX, SMAX, EMAX> &S,
+                         const int2 p, const int self, const i64 r2lo, const i64 r2hi,
+                         const bool cut_only, const int e, const int cap, const int gl, Counters &cnt) {
+    const int s = g.s;
     const int r = (int)ceilf(sqrtf((float)r2hi)) + 1;
     const int bx0 = p.x - r <= 0 ? 0 : (p.x - r) / s;
-    const int bx1 = min(P.hdr->m1 - 1, (p.x + r) / s);
+    const int bx1 = min(g.m1 - 1, (p.x + r) / s);
     const int by0 = p.y - r <= 0 ? 0 : (p.y - r) / s;
-    const int by1 = min(P.hdr->m2 - 1, (p.y + r) / s);
+    const int by1 = min(g.m2 - 1, (p.y + r) / s);
     int seen = 0;
     for (int row = by0; row <= by1; row++) {
-        const int a = P.bstart[row * P.hdr->m1 + bx0], b = P.bstart[row * P.hdr->m1 + bx1 + 1];
+        const int a = g.bs[row * g.m1 + bx0], b = g.bs[row * g.m1 + bx1 + 1];
         seen += b - a;
         for (int pos = a + gl; pos < b; pos += G) {
             if (pos == self) continue;
@@ -397,7 +397,7 @@ __device__ int scan_disc(const CellParams &P, GroupSmem<CMAX, SMAX, EMAX> &S, co
             if (at < cap) {
                 const float rc = 1.f / fc;
                 S.cand[at] = make_float4(fnx, fny, rc, (float)(abs(nx) + abs(ny)) * rc);
-                S.lab[at] = P.sid[pos];
+                S.lab[at] = P.sid[pos] - g.site_base;
             } else {
                 S.flag = 1;
             }
@@ -461,11 +461,12 @@ __device__ __forceinline__ bool cuts_vertex(const SM &S, int e, int q, int nx, i
 //      projector; with no cutter, rho doubles until it reaches 2R, where
 //      every vertex disc lies inside it and the polygon is the cell.
 template <int G, int CMAX, int SMAX, int EMAX, int RMAX>
-__device__ int certify_by_vertex_discs(const CellParams &P, GroupSmem<CMAX, SMAX, EMAX> &S,
-                                       const int2 p, const int i, i64 rho2, int &C, int &e,
-                                       const int gl, const unsigned gmask, Counters &cnt) {
-    const int s = P.hdr->s, m1 = P.hdr->m1, m2 = P.hdr->m2;
-    const i64 cxf = max(p.x, P.W - p.x), cyf = max(p.y, P.H - p.y);
+__device__ int certify_by_vertex_discs(const CellParams &P, const CellGrid &g,
+                                       GroupSmem<CMAX, SMAX, EMAX> &S, const int2 p, const int i,
+                                       i64 rho2, int &C, int &e, const int gl,
+                                       const unsigned gmask, Counters &cnt) {
+    const int s = g.s, m1 = g.m1, m2 = g.m2;
+    const i64 cxf = max(p.x, g.W - p.x), cyf = max(p.y, g.H - p.y);
     const i64 far2 = cxf * cxf + cyf * cyf;            // no site is farther than a corner
     for (int round = 0; round < 4096; round++) {
         const float R2 = polygon_vertices<G>(S, e, gl, gmask);
@@ -529,7 +530,7 @@ __device__ int certify_by_vertex_discs(const CellParams &P, GroupSmem<CMAX, SMAX
                 const int bx0 = max(0, (int)floorf(xlo / (float)s));
                 const int bx1 = min(m1 - 1, (int)floorf(xhi / (float)s));
                 if (bx0 > bx1) continue;
-                const int a = P.bstart[row * m1 + bx0], b = P.bstart[row * m1 + bx1 + 1];
+                const int a = g.bs[row * m1 + bx0], b = g.bs[row * m1 + bx1 + 1];
                 for (int pos = a + gl; pos < b; pos += G) {
                     if (pos == i) continue;
                     const int2 site = P.sxy[pos];
@@ -546,7 +547,7 @@ __device__ int certify_by_vertex_discs(const CellParams &P, GroupSmem<CMAX, SMAX
                     if (at < CMAX) {
                         const float fc = (float)cc, rc = 1.f / fc;
                         S.cand[at] = make_float4((float)nx, (float)ny, rc, (float)(abs(nx) + abs(ny)) * rc);
-                        S.lab[at] = P.sid[pos];
+                        S.lab[at] = P.sid[pos] - g.site_base;
                     } else {
                         S.flag = 1;
                     }
@@ -586,22 +587,24 @@ template <int G, int CMAX, int SMAX, int EMAX, int RMAX, bool LARGE>
 __device__ int process_cell(const CellParams &P, GroupSmem<CMAX, SMAX, EMAX> &S, int i, int gl,
                             unsigned gmask, Counters &cnt) {
     const int2 p = P.sxy[i];
-    const int k = P.sid[i];
+    const int k = P.sid[i];                            // index in the batch
+    const CellGrid g = cell_grid(P, i);
+    const int kl = k - g.site_base;                    // index in its set
 
     // ---- 1. candidates: the sites within rho of p, then the four sides --------
     // rho is chosen so that about P.target sites fall in the disc, from the
     // site density of the 3x3 buckets around p's bucket
-    const int s = P.hdr->s;
+    const int s = g.s;
     const int bx = p.x / s, by = p.y / s;
     int c9 = 0, nb9 = 0;
     {
-        const int x0 = max(bx - 1, 0), x1 = min(bx + 1, P.hdr->m1 - 1);
-        for (int row = max(by - 1, 0); row <= min(by + 1, P.hdr->m2 - 1); row++) {
-            c9 += P.bstart[row * P.hdr->m1 + x1 + 1] - P.bstart[row * P.hdr->m1 + x0];
+        const int x0 = max(bx - 1, 0), x1 = min(bx + 1, g.m1 - 1);
+        for (int row = max(by - 1, 0); row <= min(by + 1, g.m2 - 1); row++) {
+            c9 += g.bs[row * g.m1 + x1 + 1] - g.bs[row * g.m1 + x0];
             nb9 += x1 - x0 + 1;
         }
     }
-    const i64 cxf = max(p.x, P.W - p.x), cyf = max(p.y, P.H - p.y);
+    const i64 cxf = max(p.x, g.W - p.x), cyf = max(p.y, g.H - p.y);
     const i64 far2 = cxf * cxf + cyf * cyf;           // no site is farther than a corner
     const float area = (float)nb9 * (float)s * (float)s;
     i64 rho2 = (i64)((float)P.target * area / (3.14159265f * (float)max(c9 - 1, 1)));
@@ -610,7 +613,7 @@ __device__ int process_cell(const CellParams &P, GroupSmem<CMAX, SMAX, EMAX> &S,
     for (int attempt = 0;; attempt++) {
         if (gl == 0) { S.ncand = 0; S.flag = 0; }
         group_sync<G>(gmask);
-        scanned += scan_disc<G>(P, S, p, i, -1, rho2, false, 0, CMAX - 4, gl, cnt);
+        scanned += scan_disc<G>(P, g, S, p, i, -1, rho2, false, 0, CMAX - 4, gl, cnt);
         group_sync<G>(gmask);
         if (!S.flag) break;
         if (!LARGE || attempt >= 24 || rho2 <= 4) return CELL_DEFER;
@@ -618,8 +621,8 @@ __device__ int process_cell(const CellParams &P, GroupSmem<CMAX, SMAX, EMAX> &S,
     }
     int C = S.ncand;
     if (gl == 0) {
-        const int sx[4] = {0, P.W - p.x, 0, -p.x};
-        const int sy[4] = {-p.y, 0, P.H - p.y, 0};
+        const int sx[4] = {0, g.W - p.x, 0, -p.x};
+        const int sy[4] = {-p.y, 0, g.H - p.y, 0};
 #pragma unroll
         for (int q = 0; q < 4; q++) {
             const float cf = (float)(2 * ((i64)sx[q] * sx[q] + (i64)sy[q] * sy[q]));
@@ -640,8 +643,8 @@ __device__ int process_cell(const CellParams &P, GroupSmem<CMAX, SMAX, EMAX> &S,
 
     // ---- 3. security-radius certificate -------------------------------------
     if (LARGE) {
-        const int rc = certify_by_vertex_discs<G, CMAX, SMAX, EMAX, RMAX>(P, S, p, i, rho2, C, e, gl,
-                                                                          gmask, cnt);
+        const int rc = certify_by_vertex_discs<G, CMAX, SMAX, EMAX, RMAX>(P, g, S, p, i, rho2, C, e,
+                                                                          gl, gmask, cnt);
         if (rc != CELL_OK) return rc;
     }
     // every site a with |a - p|^2 > rho2 has not been looked at and is
@@ -665,7 +668,7 @@ __device__ int process_cell(const CellParams &P, GroupSmem<CMAX, SMAX, EMAX> &S,
         for (int shrink = 0;; shrink++) {
             if (gl == 0) { S.ncand = C; S.flag = 0; }
             group_sync<G>(gmask);
-            scanned += scan_disc<G>(P, S, p, i, rho2, step2, true, e, CMAX, gl, cnt);
+            scanned += scan_disc<G>(P, g, S, p, i, rho2, step2, true, e, CMAX, gl, cnt);
             group_sync<G>(gmask);
             if (!S.flag) break;
             // too many sites cut the polygon at once: test a thinner annulus
@@ -714,7 +717,7 @@ __device__ int process_cell(const CellParams &P, GroupSmem<CMAX, SMAX, EMAX> &S,
         if (qq >= e) qq -= e;
         const int lab = S.lab[S.emit[qq]];
         dst[q] = lab;
-        dcnt += lab > k ? 1 : 0;
+        dcnt += lab > kl ? 1 : 0;
     }
     dcnt = group_sum<G>(dcnt, gmask);
     if (gl == 0) {
@@ -740,7 +743,15 @@ __global__ void cells_kernel(CellParams P) {
     const int gpb = blockDim.x / G;
     const int total = P.cell_list ? *P.list_count : P.n;
     Counters cnt{};
-    for (int t = blockIdx.x * gpb + gib; t < total; t += gridDim.x * gpb) {
+    // the large-cell pass takes cells one at a time from a shared counter
+    // (their costs differ by orders of magnitude); the others stride
+    int t = LARGE ? 0 : blockIdx.x * gpb + gib;
+    for (;;) {
+        if (LARGE) {
+            if (gl == 0) t = atomicAdd(&P.hdr->large_next, 1);
+            t = __shfl_sync(gmask, t, 0, G);
+        }
+        if (t >= total) break;
         const int i = P.cell_list ? P.cell_list[t] : t;
         const int rc = process_cell<G, CMAX, SMAX, EMAX, RMAX, LARGE>(P, S, i, gl, gmask, cnt);
         if (rc != CELL_OK && gl == 0) {
@@ -753,6 +764,7 @@ __global__ void cells_kernel(CellParams P) {
             }
         }
         group_sync<G>(gmask);
+        if (!LARGE) t += gridDim.x * gpb;
     }
     if (P.collect_stats && gl == 0) {
         unsigned long long *st = P.hdr->stats;
@@ -782,16 +794,12 @@ template <int G>
 cudaError_t launch_fast_g(const CellParams &P, cudaStream_t st) {
     auto kern = cells_kernel<G, F_CMAX, F_SMAX, F_EMAX, F_RMAX, false>;
     const int smem = F_GROUPS * (int)sizeof(FastSmem);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    int resident = 0;
+    cudaError_t e = resident_grid((const void *)kern, F_GROUPS * G, smem, resident);
     if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, F_GROUPS * G, smem);
-    if (per_sm < 1) per_sm = 1;
     const int total = P.cell_list ? P.n_list : P.n;
     long long want = ((long long)total + F_GROUPS - 1) / F_GROUPS;
-    long long grid = (long long)sms * per_sm;
+    long long grid = resident;
     if (want < grid) grid = want;
     if (grid < 1) grid = 1;
     kern<<<(unsigned)grid, F_GROUPS * G, smem, st>>>(P);

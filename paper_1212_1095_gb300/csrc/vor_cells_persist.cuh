@@ -45,13 +45,14 @@ __global__ void __launch_bounds__(256) gather_kernel(CellParams P, GatherOut G, 
     if (t >= G.cap) { G.count[t] = -1; return; }
     const int i = P.cell_list ? P.cell_list[t] : t;
     const int2 p = P.sxy[i];
-    const int s = P.hdr->s;
+    const CellGrid g = cell_grid(P, i);
+    const int s = g.s;
     const int bx = p.x / s, by = p.y / s;
     int c9 = 0, nb9 = 0;
     {
-        const int x0 = max(bx - 1, 0), x1 = min(bx + 1, P.hdr->m1 - 1);
-        for (int row = max(by - 1, 0); row <= min(by + 1, P.hdr->m2 - 1); row++) {
-            c9 += P.bstart[row * P.hdr->m1 + x1 + 1] - P.bstart[row * P.hdr->m1 + x0];
+        const int x0 = max(bx - 1, 0), x1 = min(bx + 1, g.m1 - 1);
+        for (int row = max(by - 1, 0); row <= min(by + 1, g.m2 - 1); row++) {
+            c9 += g.bs[row * g.m1 + x1 + 1] - g.bs[row * g.m1 + x0];
             nb9 += x1 - x0 + 1;
         }
     }
@@ -59,12 +60,12 @@ __global__ void __launch_bounds__(256) gather_kernel(CellParams P, GatherOut G, 
     i64 rho2 = (i64)(target * area / (3.14159265f * (float)max(c9 - 1, 1)));
     rho2 = max(min(rho2, (i64)(16.f * (float)s * (float)s)), (i64)4);
     const int r = (int)ceilf(sqrtf((float)rho2)) + 1;
-    const int bx0 = p.x - r <= 0 ? 0 : (p.x - r) / s, bx1 = min(P.hdr->m1 - 1, (p.x + r) / s);
-    const int by0 = p.y - r <= 0 ? 0 : (p.y - r) / s, by1 = min(P.hdr->m2 - 1, (p.y + r) / s);
+    const int bx0 = p.x - r <= 0 ? 0 : (p.x - r) / s, bx1 = min(g.m1 - 1, (p.x + r) / s);
+    const int by0 = p.y - r <= 0 ? 0 : (p.y - r) / s, by1 = min(g.m2 - 1, (p.y + r) / s);
     int cnt = 0;
     int *dst = G.pos + (size_t)t * G.gmax;
     for (int row = by0; row <= by1; row++) {
-        const int a = P.bstart[row * P.hdr->m1 + bx0], b = P.bstart[row * P.hdr->m1 + bx1 + 1];
+        const int a = g.bs[row * g.m1 + bx0], b = g.bs[row * g.m1 + bx1 + 1];
         for (int pos = a; pos < b; pos++) {
             if (pos == i) continue;
             const int2 q = P.sxy[pos];
@@ -96,6 +97,7 @@ __global__ void __launch_bounds__(NT) cells_persist_kernel(CellParams P, GatherO
     // state of the thread's current cell
     int i = -1, C = 0;
     int2 p = make_int2(0, 0);
+    int cW = 0, cH = 0, cbase = 0;   // the cell's box and the first site of its set
     i64 rho2 = 0;
     int phase = 0, h0c = -1, h0w = -1, h1c = -1, h1w = -1;
     i64 lx = 0, ly = 0;
@@ -134,7 +136,7 @@ __global__ void __launch_bounds__(NT) cells_persist_kernel(CellParams P, GatherO
                             const float vx = (float)Nx * rd, vy = (float)Ny * rd;
                             R2 = fmaxf(R2, fmaf(vx, vx, vy * vy));
                         }
-                        const i64 cxf = max(p.x, P.W - p.x), cyf = max(p.y, P.H - p.y);
+                        const i64 cxf = max(p.x, cW - p.x), cyf = max(p.y, cH - p.y);
                         const i64 need = (i64)(4.f * (R2 * (1.f + 0x1p-12f) + 1.f)) + 1;
                         if (!(need <= rho2 || rho2 >= cxf * cxf + cyf * cyf)) defer = true;
                     }
@@ -148,6 +150,7 @@ __global__ void __launch_bounds__(NT) cells_persist_kernel(CellParams P, GatherO
                             if (angle_less(qx, qy, bxn, byn)) { start = q; bxn = qx; byn = qy; }
                         }
                         const int k = P.sid[i];
+                        const int kl = k - cbase;
                         int *dst;
                         int off = -1;
                         if (e <= SLOT_CAP) {
@@ -163,9 +166,9 @@ __global__ void __launch_bounds__(NT) cells_persist_kernel(CellParams P, GatherO
                                 int qq = start + q;
                                 if (qq >= e) qq -= e;
                                 const int c = emit[qq];
-                                const int l = c < 4 ? -1 - c : P.sid[cpos[c]];
+                                const int l = c < 4 ? -1 - c : P.sid[cpos[c]] - cbase;
                                 dst[q] = l;
-                                dcnt += l > k ? 1 : 0;
+                                dcnt += l > kl ? 1 : 0;
                             }
                             P.ecount[k] = e;
                             P.dcount[k] = dcnt;
@@ -201,9 +204,15 @@ __global__ void __launch_bounds__(NT) cells_persist_kernel(CellParams P, GatherO
                     }
                     p = P.sxy[i];
                     rho2 = G.rho2[tt];
+                    {
+                        const SetMeta &M = set_of(P.sets, P.sset, i);
+                        cW = M.W;
+                        cH = M.H;
+                        cbase = (int)M.site_base;
+                    }
                     T.put(0, t1::cand_of(0, -p.y, true));
-                    T.put(1, t1::cand_of(P.W - p.x, 0, true));
-                    T.put(2, t1::cand_of(0, P.H - p.y, true));
+                    T.put(1, t1::cand_of(cW - p.x, 0, true));
+                    T.put(2, t1::cand_of(0, cH - p.y, true));
                     T.put(3, t1::cand_of(-p.x, 0, true));
                     const int *src = G.pos + (size_t)tt * G.gmax;
                     for (int q = 0; q < nc; q++) {

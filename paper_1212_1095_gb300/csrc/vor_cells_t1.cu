@@ -11,15 +11,11 @@ static cudaError_t launch_pass(const CellParams &P, const GatherOut &G, float ta
     if (e != cudaSuccess) return e;
     auto kern = cells_persist_kernel<P_NT, CMAX, P_SMAX, P_EMAX, P_RMAX>;
     const int smem = P_NT * CMAX * (int)sizeof(float4);
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    int resident = 0;
+    e = resident_grid((const void *)kern, P_NT, smem, resident);
     if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, P_NT, smem);
-    if (per_sm < 1) per_sm = 1;
     long long want = ((long long)total_max + P_NT - 1) / P_NT;
-    long long grid = (long long)sms * per_sm;
+    long long grid = resident;
     if (want < grid) grid = want;
     if (grid < 1) grid = 1;
     kern<<<(unsigned)grid, P_NT, smem, st>>>(P, G);

@@ -1,6 +1,7 @@
 // vor_internal.h -- shared declarations of the library's translation units.
 #pragma once
 
+#include <cmath>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -15,6 +16,7 @@ enum : unsigned {
     ERRB_CAPACITY = 4u,
     ERRB_INTERNAL = 8u,
     ERRB_SPILL = 16u,
+    ERRB_ARG = 32u,          // the device copy of the set offsets disagrees with the host's
 };
 
 // per-build counters (vor_stats order)
@@ -30,20 +32,80 @@ struct WsHeader {
     int ndeferred;          // cells handed from the first to the second pass
     int ndeferred2;         // cells handed to the warp-per-cell pass
     unsigned long long stats[STAT_N];
-    int s, m1, m2, m;       // bucket side and grid (chosen on the device)
-    long long pad[10];
+    int large_next;         // next cell of the large-cell pass (dynamic schedule)
+    int m_total;            // buckets over all sets (set by the grid choice)
+    long long pad[11];
 };
 static_assert(sizeof(WsHeader) <= 256, "header");
 
 // Cells a first-pass group stores in fixed slots (larger ones spill).
 constexpr int SLOT_CAP = 16;
 
+// One point set of a batch (a single build is a batch of one set).
+struct SetMeta {
+    long long site_base;    // index of the set's first site in the batch
+    long long bucket_base;  // first bucket of the set's grid in the batch's bucket array
+    long long coarse_base;  // first cell of the set's density-probe grid
+    int n, W, H;            // sites, box [0,W] x [0,H]
+    int s, m1, m2;          // bucket side and grid (chosen on the device)
+    int G;                  // side of the density-probe grid
+    int s_min, s_max, s_fixed, m_max;
+    double acc;             // probe: sum over the set's sites of log2(coarse count)
+};
+
+// Sizes of a set's grids, computed identically on the host (workspace
+// sizing) and on the device (planning kernel).
+struct SetPlan { int s_min, s_max, m_max, G; };
+
+__host__ __device__ inline long long isqrt_floor_ll(long long v) {
+    if (v <= 0) return 0;
+    long long r = (long long)sqrt((double)v);
+    while (r * r > v) r--;
+    while ((r + 1) * (r + 1) <= v) r++;
+    return r;
+}
+
+// bucket side between s_min (at most max(4n, 4096) buckets) and s_max (the
+// side of a bucket holding 8 sites at the average density), or fixed by the
+// caller
+__host__ __device__ inline bool plan_set(long long n, int W, int H, int s_fixed, SetPlan &pl) {
+    if (n < 1 || W < 2 || H < 2 || W > (1 << 20) || H > (1 << 20)) return false;
+    if (s_fixed < 0 || s_fixed > (1 << 20)) return false;
+    const long long area = (long long)W * H;
+    const long long mcap = n * 4 > 4096 ? n * 4 : 4096;
+    long long smin = isqrt_floor_ll(area / mcap);
+    while (smin * smin * mcap < area) smin++;
+    long long smax = isqrt_floor_ll(8 * area / n);
+    if (smax < smin) smax = smin;
+    if (smax > (1 << 20)) smax = 1 << 20;
+    if (smin > (1 << 20)) smin = 1 << 20;
+    pl.s_min = (int)smin;
+    pl.s_max = (int)smax;
+    const long long sm = s_fixed > 0 ? s_fixed : smin;
+    const long long m1 = (W + sm - 1) / sm, m2 = (H + sm - 1) / sm;
+    if (m1 * m2 > (1ll << 28)) return false;
+    pl.m_max = (int)(m1 * m2);
+    long long g = isqrt_floor_ll(n) / 8;
+    pl.G = (int)(g < 16 ? 16 : (g > 1024 ? 1024 : g));
+    return true;
+}
+
+// The grid of one cell's set, for the kernels.
+struct CellGrid {
+    const int *bs;          // the set's bucket starts
+    int s, m1, m2, W, H;
+    int site_base;
+};
+
 struct CellParams {
     const int2 *sites;      // original order (device)
-    const int2 *sxy;        // sites sorted by bucket
-    const int *sid;         // original index of sorted position
-    const int *bstart;      // bucket CSR (m1*m2 + 1)
-    int n, W, H;
+    const int2 *sxy;        // sites sorted by set, then bucket
+    const int *sid;         // original (batch) index of sorted position
+    const int *bstart;      // bucket CSR over all sets
+    const SetMeta *sets;    // per-set metadata
+    const int *sset;        // set of each site (the same in sorted and original
+                            // order, as the sets stay contiguous); null: one set
+    int n;                  // sites in the batch
     int target;             // sites wanted in the first candidate disc
     int exact_only;
     int collect_stats;
@@ -60,6 +122,25 @@ struct CellParams {
     int *deferred_count;    // device counter of that list
     WsHeader *hdr;
 };
+
+__device__ __forceinline__ const SetMeta &set_of(const SetMeta *sets, const int *sset, int i) {
+    return sets[sset ? sset[i] : 0];
+}
+
+__device__ __forceinline__ CellGrid cell_grid(const CellParams &P, int i) {
+    const SetMeta &M = set_of(P.sets, P.sset, i);
+    CellGrid g;
+    g.bs = P.bstart + M.bucket_base;
+    g.s = M.s; g.m1 = M.m1; g.m2 = M.m2; g.W = M.W; g.H = M.H;
+    g.site_base = (int)M.site_base;
+    return g;
+}
+
+// Resident CTAs of a kernel on the current device (all SMs x CTAs per SM),
+// after raising its dynamic shared memory limit to smem.  Computed once per
+// device and kernel; later calls make no CUDA call, so builds can be
+// captured into a CUDA graph after a first (warm-up) build on the device.
+cudaError_t resident_grid(const void *kern, int threads, int smem, int &grid);
 
 // Launchers (vor_cells.cu)
 cudaError_t launch_cells_fast(const CellParams &P, int lanes, cudaStream_t st);

@@ -1,19 +1,25 @@
-// vor_lib.cu -- bucketing, scans, compaction and the C ABI of libvor.so.
+// vor_lib.cu -- planning, bucketing, scans, compaction and the C ABI of libvor.so.
 //
-// Pipeline of one build (all on one stream, no host synchronisation):
-//   K1  bucket_count   validate sites (interior of X, Section 2), count sites
-//                      per bucket of side s (Method A.5), record each site's
-//                      rank inside its bucket
+// A build runs a batch of independent point sets (a single diagram is a
+// batch of one set).  Pipeline (all on one stream, no host synchronisation):
+//   K0  plan           per set: box, sizes of its grids, offsets (one block)
+//       site_set       per site: its set (batches only)
+//   K1  probe          per set: site density on a coarse grid
+//       pick_grid      per set: bucket side s (Method A.5) and bucket offsets
+//       bucket_count   validate sites (interior of X, Section 2), count sites
+//                      per bucket, record each site's rank inside its bucket
 //       scan           bucket counts -> bucket start offsets
-//       bucket_scatter sites sorted by bucket (row-major), with their index
+//       bucket_scatter sites sorted by set, then bucket, with their index
 //       dup_check      equal sites share a bucket: compare within buckets
-//   K2  cells          the projector per cell (vor_cells.cu), then the
-//                      large-cell pass over the cells it deferred
+//   K2  cells          the projector per cell (vor_cells*.cu): two
+//                      thread-per-cell passes, then the large-cell pass over
+//                      the cells they deferred
 //       scan x2        e_k -> cell_ptr, Delaunay counts -> offsets
 //   K3  compact        CSR edge labels, float64 vertices (Section 5) and the
-//                      Delaunay pairs (Section 6)
+//                      Delaunay pairs (Section 6), labels local to the set
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <cuda_runtime.h>
 
 #include "vor.h"
@@ -23,34 +29,85 @@
 namespace vor {
 
 // ---------------------------------------------------------------------------
+// K0: per-set plan (a single build is a batch of one set)
+// ---------------------------------------------------------------------------
+
+// One block of SCAN_T threads: per set, its sites, box and grid sizes
+// (plan_set, the same function that sized the workspace on the host) and the
+// offsets of its density-probe grid.  The device copy of the set offsets is
+// checked against what the host planned with (hn_total, hm_sum, hg_sum): a
+// mismatch stops the build before any kernel indexes with it.
+__global__ void k_plan(const long long *__restrict__ set_ptr, const vor_box *__restrict__ boxes,
+                       int n_sets, long long n1, vor_box box1, int s_fixed, long long hn_total,
+                       long long hm_sum, long long hg_sum, SetMeta *__restrict__ sets,
+                       WsHeader *hdr);
+
+// per site: the set it belongs to (binary search in the set offsets)
+__global__ void k_site_set(const long long *__restrict__ set_ptr, int n_sets, int n,
+                           int *__restrict__ sset, const WsHeader *hdr) {
+    if (hdr->err) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int lo = 0, hi = n_sets;             // invariant: set_ptr[lo] <= i < set_ptr[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (set_ptr[mid] <= i) lo = mid;
+        else hi = mid;
+    }
+    sset[i] = lo;
+}
+
+// ---------------------------------------------------------------------------
 // K1: bucketing
 // ---------------------------------------------------------------------------
 
-// Site density probe: the bucket side is chosen so that a bucket around a
-// typical site holds about two sites.  A coarse G x G grid counts the sites;
-// the typical neighbourhood count is the geometric mean, over the sites, of
-// the count of their own coarse cell.
-__global__ void k_probe_count(const int2 *__restrict__ sites, int n, int W, int H, int G,
-                              int *__restrict__ coarse) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int2 p = sites[i];
-    if (p.x <= 0 || p.x >= W || p.y <= 0 || p.y >= H) return;   // reported by k_bucket_count
-    const int cx = (int)((long long)p.x * G / W), cy = (int)((long long)p.y * G / H);
-    atomicAdd(&coarse[cy * G + cx], 1);
+__device__ __forceinline__ bool outside(int2 p, const SetMeta &M) {
+    return p.x <= 0 || p.x >= M.W || p.y <= 0 || p.y >= M.H;
 }
 
-__global__ void k_probe_mean(const int2 *__restrict__ sites, int n, int W, int H, int G,
-                             const int *__restrict__ coarse, double *__restrict__ acc) {
-    __shared__ float sh[8];
+__device__ __forceinline__ long long bucket_of(int2 p, const SetMeta &M) {
+    return M.bucket_base + (long long)(p.y / M.s) * M.m1 + p.x / M.s;
+}
+
+// Site density probe: the bucket side is chosen so that a bucket around a
+// typical site holds about two sites.  A coarse G x G grid per set counts
+// the sites; the typical neighbourhood count is the geometric mean, over the
+// set's sites, of the count of their own coarse cell.
+__global__ void k_probe_count(const int2 *__restrict__ sites, int n, const SetMeta *__restrict__ sets,
+                              const int *__restrict__ sset, int *__restrict__ coarse,
+                              const WsHeader *hdr) {
+    if (hdr->err) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const SetMeta &M = set_of(sets, sset, i);
+    const int2 p = sites[i];
+    if (outside(p, M)) return;                              // reported by k_bucket_count
+    const int cx = (int)((long long)p.x * M.G / M.W), cy = (int)((long long)p.y * M.G / M.H);
+    atomicAdd(&coarse[M.coarse_base + (long long)cy * M.G + cx], 1);
+}
+
+__global__ void k_probe_mean(const int2 *__restrict__ sites, int n, SetMeta *__restrict__ sets,
+                             const int *__restrict__ sset, const int *__restrict__ coarse,
+                             const WsHeader *hdr) {
+    __shared__ float sh[8];
+    if (hdr->err) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j0 = sset ? sset[blockIdx.x * blockDim.x] : 0;
+    int j = j0;
     float v = 0.f;
     if (i < n) {
+        j = sset ? sset[i] : 0;
+        const SetMeta &M = sets[j];
         const int2 p = sites[i];
-        if (!(p.x <= 0 || p.x >= W || p.y <= 0 || p.y >= H)) {
-            const int cx = (int)((long long)p.x * G / W), cy = (int)((long long)p.y * G / H);
-            v = log2f((float)max(coarse[cy * G + cx], 1));
+        if (!outside(p, M)) {
+            const int cx = (int)((long long)p.x * M.G / M.W), cy = (int)((long long)p.y * M.G / M.H);
+            v = log2f((float)max(coarse[M.coarse_base + (long long)cy * M.G + cx], 1));
         }
+    }
+    // blocks inside one set reduce first; blocks across a set boundary add per site
+    if (!__syncthreads_and(j == j0)) {
+        if (v != 0.f) atomicAdd(&sets[j].acc, (double)v);
+        return;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -59,65 +116,58 @@ __global__ void k_probe_mean(const int2 *__restrict__ sites, int n, int W, int H
     if (threadIdx.x == 0) {
         float t = 0.f;
         for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += sh[w];
-        atomicAdd(acc, (double)t);
+        atomicAdd(&sets[j0].acc, (double)t);
     }
 }
 
-__global__ void k_pick_grid(const double *__restrict__ acc, int n, int W, int H, int G, int s_fixed,
-                            int s_min, int s_max, WsHeader *hdr) {
-    int s = s_fixed;
-    if (s <= 0) {
-        const double cmed = exp2(acc[0] / (double)n);    // typical sites per coarse cell
-        const double area = ((double)W / G) * ((double)H / G);
-        s = (int)sqrt(2.0 * area / cmed);
-        s = max(s_min, min(s_max, s));
-    }
-    s = max(s, 1);
-    hdr->s = s;
-    hdr->m1 = (W + s - 1) / s;
-    hdr->m2 = (H + s - 1) / s;
-    hdr->m = hdr->m1 * hdr->m2;
-}
+// One block of SCAN_T threads: per set, the bucket side (from the probe, or
+// fixed), its grid, and the offset of its buckets in the batch's bucket array.
+__global__ void k_pick_grid(SetMeta *__restrict__ sets, int n_sets, int s_fixed, WsHeader *hdr);
 
-__global__ void k_bucket_count(const int2 *__restrict__ sites, int n, int W, int H,
-                               int *__restrict__ bcount, int *__restrict__ rank, WsHeader *hdr) {
+__global__ void k_bucket_count(const int2 *__restrict__ sites, int n, const SetMeta *__restrict__ sets,
+                               const int *__restrict__ sset, int *__restrict__ bcount,
+                               int *__restrict__ rank, WsHeader *hdr) {
+    if (hdr->err) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const SetMeta &M = set_of(sets, sset, i);
     const int2 p = sites[i];
-    if (p.x <= 0 || p.x >= W || p.y <= 0 || p.y >= H) {
+    if (outside(p, M)) {
         atomicOr(&hdr->err, ERRB_OUTSIDE);
         rank[i] = -1;
         return;
     }
-    const int s = hdr->s;
-    const int b = (p.y / s) * hdr->m1 + p.x / s;
-    rank[i] = atomicAdd(&bcount[b], 1);
+    rank[i] = atomicAdd(&bcount[bucket_of(p, M)], 1);
 }
 
-__global__ void k_bucket_scatter(const int2 *__restrict__ sites, int n,
-                                 const int *__restrict__ bstart, const int *__restrict__ rank,
-                                 int2 *__restrict__ sxy, int *__restrict__ sid, const WsHeader *hdr) {
+// Sites sorted by set, then bucket (row-major inside the set's grid): the
+// sets' bucket ranges follow each other, so set j occupies the sorted
+// positions [site_base_j, site_base_j + n_j) like the original order.
+__global__ void k_bucket_scatter(const int2 *__restrict__ sites, int n, const SetMeta *__restrict__ sets,
+                                 const int *__restrict__ sset, const int *__restrict__ bstart,
+                                 const int *__restrict__ rank, int2 *__restrict__ sxy,
+                                 int *__restrict__ sid, const WsHeader *hdr) {
     if (hdr->err) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const SetMeta &M = set_of(sets, sset, i);
     const int2 p = sites[i];
-    const int s = hdr->s;
-    const int b = (p.y / s) * hdr->m1 + p.x / s;
-    const int pos = bstart[b] + rank[i];
+    const int pos = bstart[bucket_of(p, M)] + rank[i];
     sxy[pos] = p;
     sid[pos] = i;
 }
 
-// Distinct sites (Section 2): equal sites fall into the same bucket, so a
-// comparison inside each bucket finds every duplicate.
-__global__ void k_dup_check(const int2 *__restrict__ sxy, int n, const int *__restrict__ bstart,
+// Distinct sites (Section 2): equal sites of a set fall into the same
+// bucket, so a comparison inside each bucket finds every duplicate.
+__global__ void k_dup_check(const int2 *__restrict__ sxy, int n, const SetMeta *__restrict__ sets,
+                            const int *__restrict__ sset, const int *__restrict__ bstart,
                             WsHeader *hdr) {
     if (hdr->err) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const SetMeta &M = set_of(sets, sset, i);
     const int2 p = sxy[i];
-    const int s = hdr->s;
-    const int b = (p.y / s) * hdr->m1 + p.x / s;
+    const long long b = bucket_of(p, M);
     const int a = bstart[b], e = bstart[b + 1];
     for (int j = a; j < e; j++) {
         if (j == i) continue;
@@ -231,12 +281,104 @@ static void scan(const int *in, int n_max, const int *n_dev, T *out, T *partial,
 }
 
 // ---------------------------------------------------------------------------
+// K0/K1 planning kernels (single block)
+// ---------------------------------------------------------------------------
+
+__global__ void k_plan(const long long *__restrict__ set_ptr, const vor_box *__restrict__ boxes,
+                       int n_sets, long long n1, vor_box box1, int s_fixed, long long hn_total,
+                       long long hm_sum, long long hg_sum, SetMeta *__restrict__ sets,
+                       WsHeader *hdr) {
+    __shared__ long long sh[32];
+    long long gcarry = 0, mcarry = 0;
+    int bad = 0;
+    for (int j0 = 0; j0 < n_sets; j0 += SCAN_T) {
+        const int j = j0 + threadIdx.x;
+        long long g2 = 0, mm = 0;
+        SetMeta M = {};
+        if (j < n_sets) {
+            const long long a = set_ptr ? set_ptr[j] : 0, b = set_ptr ? set_ptr[j + 1] : n1;
+            const vor_box bx = boxes ? boxes[j] : box1;
+            SetPlan pl;
+            if (b < a || (j == 0 && a != 0) || !plan_set(b - a > 0 ? b - a : 1, bx.w, bx.h, s_fixed, pl)) {
+                bad = 1;
+            } else {
+                M.site_base = a;
+                M.n = (int)(b - a);
+                M.W = bx.w;
+                M.H = bx.h;
+                M.G = pl.G;
+                M.s_min = pl.s_min;
+                M.s_max = pl.s_max;
+                M.s_fixed = s_fixed;
+                M.m_max = pl.m_max;
+                g2 = (long long)pl.G * pl.G;
+                mm = pl.m_max;
+            }
+            if (j == n_sets - 1 && b != hn_total) bad = 1;
+        }
+        long long gt, mt;
+        const long long gex = block_exclusive<long long>(g2, sh, gt);
+        block_exclusive<long long>(mm, sh, mt);
+        if (j < n_sets) {
+            M.coarse_base = gcarry + gex;
+            sets[j] = M;
+        }
+        gcarry += gt;
+        mcarry += mt;
+    }
+    bad = __syncthreads_or(bad);
+    if (threadIdx.x == 0 && (bad || gcarry > hg_sum || mcarry > hm_sum)) atomicOr(&hdr->err, ERRB_ARG);
+}
+
+__global__ void k_pick_grid(SetMeta *__restrict__ sets, int n_sets, int s_fixed, WsHeader *hdr) {
+    __shared__ long long sh[32];
+    if (hdr->err) return;
+    long long carry = 0;
+    for (int j0 = 0; j0 < n_sets; j0 += SCAN_T) {
+        const int j = j0 + threadIdx.x;
+        long long m = 0;
+        int s = 1, m1 = 1, m2 = 1;
+        if (j < n_sets) {
+            const SetMeta &M = sets[j];
+            s = s_fixed;
+            if (s <= 0) {
+                if (M.n > 0) {
+                    const double cmed = exp2(M.acc / (double)M.n);   // typical sites per coarse cell
+                    const double area = ((double)M.W / M.G) * ((double)M.H / M.G);
+                    s = (int)sqrt(2.0 * area / cmed);
+                } else {
+                    s = M.s_max;
+                }
+                s = max(M.s_min, min(M.s_max, s));
+            }
+            s = max(s, 1);
+            m1 = (M.W + s - 1) / s;
+            m2 = (M.H + s - 1) / s;
+            m = (long long)m1 * m2;
+        }
+        long long total;
+        const long long ex = block_exclusive<long long>(m, sh, total);
+        if (j < n_sets) {
+            SetMeta &M = sets[j];
+            M.s = s;
+            M.m1 = m1;
+            M.m2 = m2;
+            M.bucket_base = carry + ex;
+        }
+        carry += total;
+    }
+    if (threadIdx.x == 0) hdr->m_total = (int)carry;
+}
+
+// ---------------------------------------------------------------------------
 // K3: compaction (CSR cells, float64 vertices, Delaunay pairs)
 // ---------------------------------------------------------------------------
 
 struct CompactParams {
     const int2 *sites;
-    int n, W, H;
+    int n;
+    const SetMeta *sets;
+    const int *sset;
     const int *ecount, *dcount, *loc, *slot, *spill;
     const long long *cell_ptr, *del_ptr;
     int *edge_label;
@@ -246,11 +388,12 @@ struct CompactParams {
     WsHeader *hdr;
 };
 
-// line of label `lab` of the cell of p: 2 <n, v - p> = c
-__device__ __forceinline__ void line_of(const int2 *sites, int W, int H, int2 p, int lab, int &nx,
+// line of label `lab` of the cell of p: 2 <n, v - p> = c (set_sites: the
+// sites of p's set, indexed by local label)
+__device__ __forceinline__ void line_of(const int2 *set_sites, int W, int H, int2 p, int lab, int &nx,
                                         int &ny, i64 &c) {
     if (lab >= 0) {
-        const int2 a = sites[lab];
+        const int2 a = set_sites[lab];
         nx = a.x - p.x;
         ny = a.y - p.y;
         c = (i64)nx * nx + (i64)ny * ny;
@@ -268,6 +411,10 @@ __global__ void k_compact(CompactParams Q) {
     if (Q.hdr->err) return;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= Q.n) return;
+    const SetMeta &M = set_of(Q.sets, Q.sset, k);
+    const int2 *ss = Q.sites + M.site_base;
+    const int kl = k - (int)M.site_base;                 // index inside the set
+    const int W = M.W, H = M.H;
     const int e = Q.ecount[k];
     const long long off = Q.cell_ptr[k], doff = Q.del_ptr[k];
     if (off + e > Q.edge_cap || doff + Q.dcount[k] > Q.del_cap) {
@@ -280,7 +427,7 @@ __global__ void k_compact(CompactParams Q) {
     int lab0 = src[0];
     int n0x, n0y;
     i64 c0;
-    line_of(Q.sites, Q.W, Q.H, p, lab0, n0x, n0y, c0);
+    line_of(ss, W, H, p, lab0, n0x, n0y, c0);
     int ax = n0x, ay = n0y, a_lab = lab0;
     i64 ac = c0;
     for (int q = 0; q < e; q++) {
@@ -288,7 +435,7 @@ __global__ void k_compact(CompactParams Q) {
         i64 bc;
         if (q + 1 < e) {
             b_lab = src[q + 1];
-            line_of(Q.sites, Q.W, Q.H, p, b_lab, bx, by, bc);
+            line_of(ss, W, H, p, b_lab, bx, by, bc);
         } else {
             b_lab = lab0; bx = n0x; by = n0y; bc = c0;
         }
@@ -301,17 +448,27 @@ __global__ void k_compact(CompactParams Q) {
         Q.vx[off + q] = (double)numx / (double)D;
         Q.vy[off + q] = (double)numy / (double)D;
         // Delaunay pair (k, a) for a > k at rank = number of smaller such labels
-        if (a_lab > k) {
+        if (a_lab > kl) {
             int rank = 0;
             for (int r = 0; r < e; r++) {
                 const int o = src[r];
-                rank += (o > k && o < a_lab) ? 1 : 0;
+                rank += (o > kl && o < a_lab) ? 1 : 0;
             }
-            Q.del_edge[2 * (doff + rank)] = k;
+            Q.del_edge[2 * (doff + rank)] = kl;
             Q.del_edge[2 * (doff + rank) + 1] = a_lab;
         }
         ax = bx; ay = by; ac = bc; a_lab = b_lab;
     }
+}
+
+// per set: offset of its Delaunay pairs (out[n_sets] = total)
+__global__ void k_set_del_ptr(const SetMeta *__restrict__ sets, int n_sets, int n,
+                              const long long *__restrict__ del_ptr, long long *__restrict__ out,
+                              const WsHeader *hdr) {
+    if (hdr->err) return;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j > n_sets) return;
+    out[j] = del_ptr[j < n_sets ? sets[j].site_base : n];
 }
 
 // ---------------------------------------------------------------------------
@@ -319,65 +476,59 @@ __global__ void k_compact(CompactParams Q) {
 // ---------------------------------------------------------------------------
 
 struct Layout {
-    int s_fixed, s_min, s_max, m_max, G, lanes, target;
-    size_t hdr, bstart, rank, sxy, sid, partial, ecount, dcount, loc, del_ptr, slot, spill,
-        deferred, deferred2, gcount, grho2, gpos, coarse, total;
+    int s_fixed, lanes, target, n_sets;
+    long long n, m_sum, g_sum;
+    size_t hdr, sets, sset, bstart, rank, sxy, sid, partial, ecount, dcount, loc, del_ptr, slot,
+        spill, deferred, deferred2, gcount, grho2, gpos, coarse, total;
     int spill_cap;
     int n_partial;
 };
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-static long long isqrt_floor(long long v) {
-    if (v <= 0) return 0;
-    long long r = (long long)__builtin_sqrt((double)v);
-    while (r * r > v) r--;
-    while ((r + 1) * (r + 1) <= v) r++;
-    return r;
-}
-
-static bool resolve(int64_t n, vor_box box, const vor_opts *o, Layout &L) {
-    if (n < 1 || n > (1 << 27)) return false;
-    if (box.w < 2 || box.h < 2 || box.w > (1 << 20) || box.h > (1 << 20)) return false;
+// Sizes of the workspace of a batch (set_ptr null: one set of n1 sites in
+// box1).  Every per-set size comes from plan_set, which the planning kernel
+// evaluates again on the device.
+static bool resolve(const int64_t *set_ptr, const vor_box *boxes, int n_sets, int64_t n1,
+                    vor_box box1, const vor_opts *o, Layout &L) {
     vor_opts d;
     vor_opts_default(&d);
     if (!o) o = &d;
-    // bucket side: chosen on the device from the site density (k_pick_grid),
-    // between s_min (at most max(4n, 4096) buckets) and s_max (a quarter of
-    // the average density); or fixed by the caller
-    const long long area = (long long)box.w * box.h;
-    const long long mcap = n * 4 > 4096 ? n * 4 : 4096;
-    L.s_min = (int)isqrt_floor(area / mcap);
-    while ((long long)L.s_min * L.s_min * mcap < area) L.s_min++;
-    L.s_max = (int)isqrt_floor(8 * area / n);
-    if (L.s_max < L.s_min) L.s_max = L.s_min;
-    if (L.s_max > (1 << 20)) L.s_max = 1 << 20;
+    if (n_sets < 1 || n_sets > (1 << 24)) return false;
     L.s_fixed = 0;
     if (o->bucket_side > 0) {
         if (o->bucket_side > (1 << 20)) return false;
         L.s_fixed = o->bucket_side;
     }
-    {
-        const int smallest = L.s_fixed > 0 ? L.s_fixed : L.s_min;
-        const long long m1 = (box.w + smallest - 1) / smallest, m2 = (box.h + smallest - 1) / smallest;
-        if (m1 * m2 > (1ll << 28)) return false;
-        L.m_max = (int)(m1 * m2);
+    L.n_sets = n_sets;
+    L.m_sum = 0;
+    L.g_sum = 0;
+    if (set_ptr && set_ptr[0] != 0) return false;
+    for (int j = 0; j < n_sets; j++) {
+        const int64_t a = set_ptr ? set_ptr[j] : 0, b = set_ptr ? set_ptr[j + 1] : n1;
+        const vor_box bx = boxes ? boxes[j] : box1;
+        if (b < a) return false;
+        if (!set_ptr && b < 1) return false;
+        SetPlan pl;
+        if (!plan_set(b - a > 0 ? b - a : 1, bx.w, bx.h, L.s_fixed, pl)) return false;
+        L.m_sum += pl.m_max;
+        L.g_sum += (long long)pl.G * pl.G;
     }
-    {
-        long long g = isqrt_floor(n) / 8;
-        L.G = (int)(g < 16 ? 16 : (g > 1024 ? 1024 : g));
-    }
+    L.n = set_ptr ? set_ptr[n_sets] : n1;
+    if (L.n < 0 || L.n > (1 << 27) || L.m_sum > (1ll << 30)) return false;
     L.lanes = o->lanes_per_cell > 0 ? o->lanes_per_cell : 1;
     if (L.lanes != 1 && L.lanes != 2 && L.lanes != 4 && L.lanes != 8 && L.lanes != 16 && L.lanes != 32) return false;
     L.target = o->target > 0 ? o->target : 22;
     if (L.target > 40) return false;
-    const size_t m = (size_t)L.m_max;
-    const size_t nn = (size_t)n;
+    const size_t m = (size_t)L.m_sum;
+    const size_t nn = (size_t)(L.n > 0 ? L.n : 1);
     const int nb_b = (int)((m + SCAN_TILE - 1) / SCAN_TILE), nb_n = (int)((nn + SCAN_TILE - 1) / SCAN_TILE);
     L.n_partial = (nb_b > nb_n ? nb_b : nb_n) + 1;
     L.spill_cap = (int)(nn * 10 < (1u << 30) ? nn * 10 : (1u << 30));
     size_t at = 0;
     L.hdr = at;      at = align256(at + 256);
+    L.sets = at;     at = align256(at + (size_t)n_sets * sizeof(SetMeta));
+    L.sset = at;     at = align256(at + (set_ptr ? nn * 4 : 0));
     L.bstart = at;   at = align256(at + (m + 1) * 4);
     L.rank = at;     at = align256(at + nn * 4);
     L.sxy = at;      at = align256(at + nn * 8);
@@ -394,14 +545,14 @@ static bool resolve(int64_t n, vor_box box, const vor_opts *o, Layout &L) {
     L.gcount = at;   at = align256(at + nn * 4);
     L.grho2 = at;    at = align256(at + nn * 8);
     L.gpos = at;     at = align256(at + nn * 4 * (size_t)pass_gather_width());
-    L.coarse = at;   at = align256(at + align256((size_t)L.G * L.G * 4) + 256);
+    L.coarse = at;   at = align256(at + (size_t)L.g_sum * 4);
     L.total = at;
     return true;
 }
 
 // stage timing (vor_stage_timing / vor_stage_ms)
 static bool g_timing = false;
-static cudaEvent_t g_ev[5];
+static cudaEvent_t g_ev[6];
 static bool g_ev_made = false;
 static bool g_ev_recorded = false;
 
@@ -409,14 +560,25 @@ static void mark(int i, cudaStream_t st) {
     if (g_timing) cudaEventRecord(g_ev[i], st);
 }
 
-static int launch_build(const vor_site *d_sites, int64_t n64, vor_box box, const vor_opts *o,
-                        void *ws, const Layout &L, const vor_out *out, cudaStream_t st) {
+struct BatchArgs {
+    const int2 *sites;
+    const long long *set_ptr;   // device; null: one set
+    const vor_box *boxes;       // device; null: one set
+    long long n1;
+    vor_box box1;
+    long long *del_set_ptr;     // device output; may be null for one set
+};
+
+static int launch_build(const BatchArgs &A, const vor_opts *o, void *ws, const Layout &L,
+                        const vor_out *out, cudaStream_t st) {
     vor_opts d;
     vor_opts_default(&d);
     if (!o) o = &d;
-    const int n = (int)n64;
+    const int n = (int)L.n;
     char *base = (char *)ws;
     WsHeader *hdr = (WsHeader *)(base + L.hdr);
+    SetMeta *sets = (SetMeta *)(base + L.sets);
+    int *sset = A.set_ptr ? (int *)(base + L.sset) : nullptr;
     int *bstart = (int *)(base + L.bstart);
     int *rank = (int *)(base + L.rank);
     int2 *sxy = (int2 *)(base + L.sxy);
@@ -430,34 +592,46 @@ static int launch_build(const vor_site *d_sites, int64_t n64, vor_box box, const
     int *spill = (int *)(base + L.spill);
     int *deferred = (int *)(base + L.deferred);
     int *deferred2 = (int *)(base + L.deferred2);
-    const int2 *sites = (const int2 *)d_sites;
-    const int m = L.m_max;
+    int *coarse = (int *)(base + L.coarse);
+    const int2 *sites = A.sites;
 
     mark(0, st);
     if (cudaMemsetAsync(hdr, 0, 256, st) != cudaSuccess) return VOR_E_CUDA;
-    if (cudaMemsetAsync(bstart, 0, (size_t)(m + 1) * 4, st) != cudaSuccess) return VOR_E_CUDA;
+    k_plan<<<1, SCAN_T, 0, st>>>(A.set_ptr, A.boxes, L.n_sets, A.n1, A.box1, L.s_fixed, L.n,
+                                 L.m_sum, L.g_sum, sets, hdr);
+    if (n == 0) {
+        // nothing but empty sets: empty outputs
+        if (cudaMemsetAsync(out->cell_ptr, 0, 8, st) != cudaSuccess ||
+            cudaMemsetAsync(out->totals, 0, 16, st) != cudaSuccess ||
+            (A.del_set_ptr &&
+             cudaMemsetAsync(A.del_set_ptr, 0, (size_t)(L.n_sets + 1) * 8, st) != cudaSuccess))
+            return VOR_E_CUDA;
+        for (int i = 1; i < 6; i++) mark(i, st);
+        if (g_timing) g_ev_recorded = true;
+        return cudaGetLastError() == cudaSuccess ? VOR_OK : VOR_E_CUDA;
+    }
+    if (cudaMemsetAsync(bstart, 0, (size_t)(L.m_sum + 1) * 4, st) != cudaSuccess) return VOR_E_CUDA;
     const int T = 256;
     const int gn = (n + T - 1) / T;
-    int *coarse = (int *)(base + L.coarse);
-    double *acc = (double *)(base + L.coarse + align256((size_t)L.G * L.G * 4));
+    if (sset) k_site_set<<<gn, T, 0, st>>>(A.set_ptr, L.n_sets, n, sset, hdr);
     if (L.s_fixed <= 0) {
-        if (cudaMemsetAsync(coarse, 0, align256((size_t)L.G * L.G * 4) + 256, st) != cudaSuccess)
-            return VOR_E_CUDA;
-        k_probe_count<<<gn, T, 0, st>>>(sites, n, box.w, box.h, L.G, coarse);
-        k_probe_mean<<<gn, T, 0, st>>>(sites, n, box.w, box.h, L.G, coarse, acc);
+        if (cudaMemsetAsync(coarse, 0, (size_t)L.g_sum * 4, st) != cudaSuccess) return VOR_E_CUDA;
+        k_probe_count<<<gn, T, 0, st>>>(sites, n, sets, sset, coarse, hdr);
+        k_probe_mean<<<gn, T, 0, st>>>(sites, n, sets, sset, coarse, hdr);
     }
-    k_pick_grid<<<1, 1, 0, st>>>(acc, n, box.w, box.h, L.G, L.s_fixed, L.s_min, L.s_max, hdr);
-    k_bucket_count<<<gn, T, 0, st>>>(sites, n, box.w, box.h, bstart, rank, hdr);
-    scan<int>(bstart, m, &hdr->m, bstart, (int *)partial, nullptr, hdr, st);
-    k_bucket_scatter<<<gn, T, 0, st>>>(sites, n, bstart, rank, sxy, sid, hdr);
-    if (o->check_duplicates) k_dup_check<<<gn, T, 0, st>>>(sxy, n, bstart, hdr);
+    k_pick_grid<<<1, SCAN_T, 0, st>>>(sets, L.n_sets, L.s_fixed, hdr);
+    k_bucket_count<<<gn, T, 0, st>>>(sites, n, sets, sset, bstart, rank, hdr);
+    scan<int>(bstart, (int)L.m_sum, &hdr->m_total, bstart, (int *)partial, nullptr, hdr, st);
+    k_bucket_scatter<<<gn, T, 0, st>>>(sites, n, sets, sset, bstart, rank, sxy, sid, hdr);
+    if (o->check_duplicates) k_dup_check<<<gn, T, 0, st>>>(sxy, n, sets, sset, bstart, hdr);
     if (cudaGetLastError() != cudaSuccess) return VOR_E_CUDA;
     mark(1, st);
 
     CellParams P;
     memset(&P, 0, sizeof(P));
     P.sites = sites; P.sxy = sxy; P.sid = sid; P.bstart = bstart;
-    P.n = n; P.W = box.w; P.H = box.h;
+    P.sets = sets; P.sset = sset;
+    P.n = n;
     P.target = L.target; P.exact_only = o->exact_only; P.collect_stats = o->collect_stats;
     P.ecount = ecount; P.dcount = dcount; P.loc = loc; P.slot = slot; P.spill = spill;
     P.spill_cap = L.spill_cap;
@@ -480,11 +654,13 @@ static int launch_build(const vor_site *d_sites, int64_t n64, vor_box box, const
         P2.deferred = deferred2;
         P2.deferred_count = &hdr->ndeferred2;
         if (launch_cells_pass(P2, 2, gcount, grho2, gpos, st) != cudaSuccess) return VOR_E_CUDA;
+        mark(3, st);
     } else {
         P.deferred = deferred2;
         P.deferred_count = &hdr->ndeferred2;
         if (launch_cells_fast(P, L.lanes, st) != cudaSuccess) return VOR_E_CUDA;
         mark(2, st);
+        mark(3, st);
     }
     // warp per cell, large capacities, for what is left
     CellParams PL = P;
@@ -494,25 +670,57 @@ static int launch_build(const vor_site *d_sites, int64_t n64, vor_box box, const
     PL.deferred = nullptr;
     PL.deferred_count = nullptr;
     if (launch_cells_large(PL, n, st) != cudaSuccess) return VOR_E_CUDA;
-    mark(3, st);
+    mark(4, st);
 
     scan<long long>(ecount, n, nullptr, (long long *)out->cell_ptr, partial, (long long *)out->totals,
                     hdr, st);
     scan<long long>(dcount, n, nullptr, del_ptr, partial, (long long *)out->totals + 1, hdr, st);
     CompactParams Q;
-    Q.sites = sites; Q.n = n; Q.W = box.w; Q.H = box.h;
+    Q.sites = sites; Q.n = n; Q.sets = sets; Q.sset = sset;
     Q.ecount = ecount; Q.dcount = dcount; Q.loc = loc; Q.slot = slot; Q.spill = spill;
     Q.cell_ptr = (const long long *)out->cell_ptr; Q.del_ptr = del_ptr;
     Q.edge_label = out->edge_label; Q.vx = out->vx; Q.vy = out->vy; Q.del_edge = out->del_edge;
     Q.edge_cap = out->edge_cap; Q.del_cap = out->del_cap; Q.hdr = hdr;
     k_compact<<<gn, T, 0, st>>>(Q);
+    if (A.del_set_ptr)
+        k_set_del_ptr<<<(L.n_sets + 1 + T - 1) / T, T, 0, st>>>(sets, L.n_sets, n, del_ptr,
+                                                                 A.del_set_ptr, hdr);
     if (cudaGetLastError() != cudaSuccess) return VOR_E_CUDA;
-    mark(4, st);
+    mark(5, st);
     if (g_timing) g_ev_recorded = true;
     return VOR_OK;
 }
 
+cudaError_t resident_grid(const void *kern, int threads, int smem, int &grid) {
+    struct Entry { const void *kern; int dev, threads, smem, grid; };
+    static std::mutex mu;
+    static Entry table[256];
+    static int used = 0;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    for (int i = 0; i < used; i++) {
+        const Entry &t = table[i];
+        if (t.kern == kern && t.dev == dev && t.threads == threads && t.smem == smem) {
+            grid = t.grid;
+            return cudaSuccess;
+        }
+    }
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    int sms = 0, per_sm = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+    if (e != cudaSuccess) return e;
+    grid = sms * (per_sm < 1 ? 1 : per_sm);
+    if (used < 256) table[used++] = Entry{kern, dev, threads, smem, grid};
+    return cudaSuccess;
+}
+
 static int map_err(unsigned e) {
+    if (e & ERRB_ARG) return VOR_E_INVALID_ARG;
     if (e & ERRB_OUTSIDE) return VOR_E_SITE_OUTSIDE;
     if (e & ERRB_DUPLICATE) return VOR_E_DUPLICATE;
     if (e & ERRB_INTERNAL) return VOR_E_INTERNAL;
@@ -542,21 +750,62 @@ int64_t vor_delaunay_capacity(int64_t n) { return n < 3 ? 1 : 3 * n; }
 
 int64_t vor_workspace_bytes(int64_t n, vor_box box, const vor_opts *opts) {
     Layout L;
-    if (!resolve(n, box, opts, L)) return -1;
+    if (!resolve(nullptr, nullptr, 1, n, box, opts, L)) return -1;
     return (int64_t)L.total;
+}
+
+static bool out_ok(const vor_out *out) {
+    return out && out->cell_ptr && out->edge_label && out->vx && out->vy && out->del_edge && out->totals;
 }
 
 int vor_build_async(const vor_site *d_sites, int64_t n, vor_box box, const vor_opts *opts,
                     void *d_workspace, int64_t ws_bytes, const vor_out *out, void *stream) {
-    if (!d_sites || !d_workspace || !out || !out->cell_ptr || !out->edge_label || !out->vx ||
-        !out->vy || !out->del_edge || !out->totals)
-        return VOR_E_INVALID_ARG;
+    if (!d_sites || !d_workspace || !out_ok(out)) return VOR_E_INVALID_ARG;
     if (box.w < 2 || box.h < 2 || box.w > (1 << 20) || box.h > (1 << 20)) return VOR_E_BOX_TOO_LARGE;
     Layout L;
-    if (!resolve(n, box, opts, L)) return VOR_E_INVALID_ARG;
+    if (!resolve(nullptr, nullptr, 1, n, box, opts, L)) return VOR_E_INVALID_ARG;
     if (ws_bytes < (int64_t)L.total || ((uintptr_t)d_workspace & 255)) return VOR_E_OOM;
     if (out->edge_cap < 1 || out->del_cap < 1) return VOR_E_OOM;
-    return launch_build(d_sites, n, box, opts, d_workspace, L, out, (cudaStream_t)stream);
+    BatchArgs A = {(const int2 *)d_sites, nullptr, nullptr, n, box, nullptr};
+    return launch_build(A, opts, d_workspace, L, out, (cudaStream_t)stream);
+}
+
+int64_t vor_batch_edge_capacity(int64_t n_total, int32_t n_sets) {
+    return n_total < 0 || n_sets < 1 ? 0 : 10 * n_total + 4 * (int64_t)n_sets;
+}
+
+int64_t vor_batch_delaunay_capacity(int64_t n_total, int32_t n_sets) {
+    return n_total < 0 || n_sets < 1 ? 0 : 3 * n_total + n_sets;
+}
+
+int64_t vor_batch_workspace_bytes(const int64_t *h_set_ptr, int32_t n_sets, const vor_box *h_boxes,
+                                  const vor_opts *opts) {
+    if (!h_set_ptr || !h_boxes) return -1;
+    Layout L;
+    if (!resolve(h_set_ptr, h_boxes, n_sets, 0, vor_box{0, 0}, opts, L)) return -1;
+    return (int64_t)L.total;
+}
+
+int vor_build_batch_async(const vor_site *d_sites, const int64_t *d_set_ptr,
+                          const int64_t *h_set_ptr, int32_t n_sets, const vor_box *d_boxes,
+                          const vor_box *h_boxes, const vor_opts *opts, void *d_workspace,
+                          int64_t ws_bytes, const vor_out *out, int64_t *d_del_set_ptr,
+                          void *stream) {
+    if (!d_set_ptr || !h_set_ptr || !d_boxes || !h_boxes || !d_workspace || !out_ok(out) ||
+        !d_del_set_ptr || n_sets < 1)
+        return VOR_E_INVALID_ARG;
+    for (int j = 0; j < n_sets; j++) {
+        const vor_box b = h_boxes[j];
+        if (b.w < 2 || b.h < 2 || b.w > (1 << 20) || b.h > (1 << 20)) return VOR_E_BOX_TOO_LARGE;
+    }
+    Layout L;
+    if (!resolve(h_set_ptr, h_boxes, n_sets, 0, vor_box{0, 0}, opts, L)) return VOR_E_INVALID_ARG;
+    if (L.n > 0 && !d_sites) return VOR_E_INVALID_ARG;
+    if (ws_bytes < (int64_t)L.total || ((uintptr_t)d_workspace & 255)) return VOR_E_OOM;
+    if (out->edge_cap < 1 || out->del_cap < 1) return VOR_E_OOM;
+    BatchArgs A = {(const int2 *)d_sites, (const long long *)d_set_ptr, d_boxes, 0, vor_box{0, 0},
+                   (long long *)d_del_set_ptr};
+    return launch_build(A, opts, d_workspace, L, out, (cudaStream_t)stream);
 }
 
 int vor_status(const void *d_workspace, void *stream, vor_stats *stats) {
@@ -688,7 +937,7 @@ int vor_build_host(const vor_site *h_sites, int64_t n, vor_box box, const vor_op
 
 int vor_stage_timing(int enable) {
     if (enable && !g_ev_made) {
-        for (int i = 0; i < 5; i++)
+        for (int i = 0; i < 6; i++)
             if (cudaEventCreate(&g_ev[i]) != cudaSuccess) return VOR_E_CUDA;
         g_ev_made = true;
     }
@@ -700,9 +949,9 @@ int vor_stage_timing(int enable) {
 int vor_stage_ms(float *ms, int max_stages) {
     if (!ms || max_stages < 1) return VOR_E_INVALID_ARG;
     if (!g_ev_made || !g_ev_recorded) return VOR_E_INVALID_ARG;
-    if (cudaEventSynchronize(g_ev[4]) != cudaSuccess) return VOR_E_CUDA;
+    if (cudaEventSynchronize(g_ev[5]) != cudaSuccess) return VOR_E_CUDA;
     int k = 0;
-    for (int i = 0; i < 4 && k < max_stages; i++, k++)
+    for (int i = 0; i < 5 && k < max_stages; i++, k++)
         if (cudaEventElapsedTime(&ms[i], g_ev[i], g_ev[i + 1]) != cudaSuccess) return VOR_E_CUDA;
     return k;
 }
@@ -710,7 +959,7 @@ int vor_stage_ms(float *ms, int max_stages) {
 const char *vor_strerror(int code) {
     switch (code) {
     case VOR_OK: return "ok";
-    case VOR_E_INVALID_ARG: return "invalid argument";
+    case VOR_E_INVALID_ARG: return "invalid argument (or set offsets that differ between host and device)";
     case VOR_E_SITE_OUTSIDE: return "a site lies on or outside the boundary of the box";
     case VOR_E_DUPLICATE: return "two sites are equal";
     case VOR_E_BOX_TOO_LARGE: return "box side outside [2, 2^20]";
