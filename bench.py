@@ -34,7 +34,6 @@ if ROOT not in sys.path:
 METRIC = "cells/s at n=1M uniform; batched sets/s and p50/p99 latency vs plain"
 BOX = 1 << 20
 WORKLOADS = {"uniform_1m": 1 << 20, "gauss_4m": 1 << 22}
-KERNEL_LAUNCHES_PER_STEP = 17   # our kernels per build (see vor_lib.cu pipeline)
 OPS_PER_EVAL = 8                # FP32/ALU operations of one filter evaluation of a candidate
 
 
@@ -141,16 +140,17 @@ def measured_peaks():
 
 
 def traffic_from_profiles(workload: str):
-    """DRAM bytes per launch of the projector kernel from the committed ncu
-    summary, when one exists for this workload and the current kernel."""
-    p = os.path.join(ROOT, "profiles", f"cells_kernel_{workload}.json")
+    """DRAM bytes per launch of the first-pass projector kernel from the
+    committed ncu summary, when one exists for this workload and the kernel's
+    source files are unchanged since the capture."""
+    p = os.path.join(ROOT, "profiles", f"cells_persist_kernel_p1_{workload}.json")
     if not os.path.exists(p):
         return None
     try:
         with open(p) as f:
             d = json.load(f)
         from paper_1212_1095_gb300 import _build
-        if d.get("source_fingerprint") != _build._fingerprint():
+        if d.get("kernel_fingerprint") != _build.kernel_fingerprint(d.get("kernel_sources", [])):
             return None
         return d.get("dram_bytes_per_launch")
     except Exception:
@@ -163,18 +163,24 @@ def cpu_baseline(xy, seconds_target: float = 15.0):
     import oracle
     cores = os.cpu_count() or 1
     n = xy.shape[0]
-    probe = np.arange(0, n, max(1, n // 4096))[:4096]
-    t0 = time.perf_counter()
-    oracle.cells(xy, BOX, "bucketed", sel=probe, nthreads=cores)
-    dt = time.perf_counter() - t0
-    per_cell = dt / len(probe)
-    m = int(min(n, max(len(probe), seconds_target / max(per_cell, 1e-9))))
-    sel = np.arange(0, n, max(1, n // m))[:m]
+    # per-cell cost from two probe sizes (each call also buckets all n sites)
+    times = []
+    for k in (4096, 16384):
+        probe = np.arange(0, n, max(1, n // k))[:k]
+        t0 = time.perf_counter()
+        oracle.cells(xy, BOX, "bucketed", sel=probe, nthreads=cores)
+        times.append((len(probe), time.perf_counter() - t0))
+    (k1, t1), (k2, t2) = times
+    per_cell = max((t2 - t1) / max(k2 - k1, 1), 1e-9)
+    setup = max(t1 - k1 * per_cell, 0.0)
+    m = int(min(n, max(k2, (seconds_target - setup) / per_cell)))
+    stride = max(1, n // m)
+    sel = np.arange(0, n, stride)[:m]
     t0 = time.perf_counter()
     oracle.cells(xy, BOX, "bucketed", sel=sel, nthreads=cores)
     dt = time.perf_counter() - t0
     return {"value": len(sel) / dt, "unit": "cells/s", "cores": cores, "kind": "oracle",
-            "sample": f"{len(sel)} of {n} cells (every {max(1, n // m)}th), bucketed oracle "
+            "sample": f"{len(sel)} of {n} cells (stride {stride}), bucketed oracle "
                       f"(Method A.6), {cores} threads, {dt:.1f} s"}
 
 
@@ -253,6 +259,7 @@ def run_ours(args):
     clocks = Clocks(local)
     clocks.start()
     step_ms, cells_ms, stage_acc = [], [], []
+    launches0 = vg.vor_kernel_launches()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     for _ in range(args.steps):
@@ -263,9 +270,10 @@ def run_ours(args):
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
         st_ms = vg.vor_stage_ms()
-        cells_ms.append(st_ms[1])
+        cells_ms.append(st_ms[2])
         stage_acc.append(st_ms)
     torch.cuda.synchronize()
+    launches = vg.vor_kernel_launches() - launches0
     barrier(ws_n)
     clk = clocks.stop()
     rc, _ = vg.vor_status(W.ws_ptr, stream.cuda_stream)
@@ -325,11 +333,12 @@ def run_ours(args):
     sm_mhz = clk.get("sm_mhz") or 1920.0
     peak = props.multi_processor_count * 128 * sm_mhz * 1e6 / 1e12
     kms = sum(cells_ms) / len(cells_ms)
-    achieved = stats["evals"] * OPS_PER_EVAL / (kms / 1000.0) / 1e12
+    evals1 = stats["evals_first_pass"] if args.lanes in (0, 1) else stats["evals"]
+    achieved = evals1 * OPS_PER_EVAL / (kms / 1000.0) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TOP/s",
                 "frac": achieved / peak, "traffic": traffic_from_profiles(args.workload),
-                "kernel": "cells_thread_kernel (projector, first pass)",
-                "kernel_ms": kms, "evals_per_launch": stats["evals"],
+                "kernel": "cells_persist_kernel<64,44> (projector, first pass)",
+                "kernel_ms": kms, "evals_per_launch": evals1,
                 "ops_per_eval": OPS_PER_EVAL,
                 "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x "
                               f"{sm_mhz:.0f} MHz median SM clock (1 op per lane per cycle)"}
@@ -344,16 +353,13 @@ def run_ours(args):
                    "l2": "256 MiB buffer written between timed steps",
                    "edges": n_edges, "delaunay_edges": n_del,
                    "parallelism": f"replicas x{ws_n}" if ws_n > 1 else "1 GPU"},
-        "stages_ms": {"bucketing": statistics.mean(x[0] for x in stage_acc),
-                      "projector_first_pass": kms,
-                      "projector_second_pass": statistics.mean(x[2] for x in stage_acc),
-                      "projector_large_cells": statistics.mean(x[3] for x in stage_acc),
-                      "compaction": statistics.mean(x[4] for x in stage_acc), "step": ms},
+        "stages_ms": dict({k: statistics.mean(x[i] for x in stage_acc)
+                           for i, k in enumerate(vg.STAGES)}, step=ms),
         "stats": stats,
         "roofline": roofline,
         "clocks": clk,
         "e2e": e2e,
-        "gpu_launches": KERNEL_LAUNCHES_PER_STEP * args.steps,
+        "gpu_launches": launches,
     }
     if ws_n == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(xy)

@@ -90,7 +90,9 @@ typedef struct vor_stats {
     uint64_t candidates;       /* candidate sites staged, summed over cells                */
     uint64_t max_edges;        /* largest e_k                                              */
     uint64_t widenings;        /* certificate steps that grew the tested region            */
-    uint64_t reserved[6];
+    uint64_t evals_first_pass; /* the part of evals done by the first thread-per-cell pass */
+    uint64_t rays_first_pass;  /* the part of rays shot by the first thread-per-cell pass  */
+    uint64_t reserved[4];
 } vor_stats;
 
 /* Device output buffers, allocated by the caller with the capacities below:
@@ -169,13 +171,15 @@ int vor_build_host(const vor_site *h_sites, int64_t n, vor_box box, const vor_op
 /* Stage timing, off by default.  When enabled, vor_build_async records a
  * CUDA event on its stream before and after each stage; vor_stage_ms then
  * waits for the last event and writes the device milliseconds of the last
- * timed build: ms[0] bucketing (density probe, validation, count, scan,
- * scatter, duplicate check), ms[1] the first projector pass, ms[2] the second
- * pass, ms[3] the large-cell pass, ms[4] compaction (two scans and the
- * CSR/Delaunay kernel).  Returns the number
- * of values written (<= max_stages) or a negative VOR_E_* code.  One process
- * wide set of events on the current device: meant for benchmarking one build
- * at a time. */
+ * timed build: ms[0] planning and bucketing (density probe, validation,
+ * count, scan, scatter, duplicate check), ms[1] the candidate gather of the
+ * first thread-per-cell pass, ms[2] that pass's projector kernel, ms[3] the
+ * second pass (gather and projector), ms[4] the large-cell pass, ms[5]
+ * compaction (two scans and the CSR/Delaunay kernel).  With lanes_per_cell
+ * > 1, ms[2] is the multi-lane pass and ms[1], ms[3] are zero.  Returns the
+ * number of values written (<= max_stages) or a negative VOR_E_* code.  One
+ * process-wide set of events on the current device: meant for benchmarking
+ * one build at a time. */
 int vor_stage_timing(int enable);
 int vor_stage_ms(float *ms, int max_stages);
 
@@ -253,6 +257,10 @@ int vor_build_batch_async(const vor_site *d_sites, const int64_t *d_set_ptr,
                           const vor_box *h_boxes, const vor_opts *opts, void *d_workspace,
                           int64_t ws_bytes, const vor_out *out, int64_t *d_del_set_ptr,
                           void *stream);
+
+/* Number of kernels this library has launched in this process (all builds,
+ * all devices; a captured CUDA graph's replays are not counted). */
+int64_t vor_kernel_launches(void);
 
 /* Human-readable text of a VOR_* code. */
 const char *vor_strerror(int code);

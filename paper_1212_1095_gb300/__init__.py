@@ -22,9 +22,9 @@ __all__ = ["VorOpts", "VorStats", "VorOut", "VorError", "build_library", "librar
            "vor_opts_default", "vor_workspace_bytes", "vor_build_async", "vor_status",
            "vor_edge_capacity", "vor_delaunay_capacity", "vor_host_scratch_bytes",
            "vor_build_host", "vor_build_noalloc", "vor_strerror", "vor_stage_timing",
-           "vor_stage_ms", "build", "build_host", "Diagram", "vor_batch_edge_capacity",
+           "vor_stage_ms", "STAGES", "build", "build_host", "Diagram", "vor_batch_edge_capacity",
            "vor_batch_delaunay_capacity", "vor_batch_workspace_bytes", "vor_build_batch_async",
-           "BatchWorkspace", "BatchDiagram", "build_batch",
+           "BatchWorkspace", "BatchDiagram", "build_batch", "vor_kernel_launches",
            "SIDE_BOTTOM", "SIDE_RIGHT", "SIDE_TOP", "SIDE_LEFT"]
 
 SIDE_BOTTOM, SIDE_RIGHT, SIDE_TOP, SIDE_LEFT = -1, -2, -3, -4
@@ -61,7 +61,8 @@ class VorStats(ctypes.Structure):
                 ("annulus_sites", ctypes.c_uint64), ("reruns", ctypes.c_uint64),
                 ("deferred", ctypes.c_uint64), ("candidates", ctypes.c_uint64),
                 ("max_edges", ctypes.c_uint64), ("widenings", ctypes.c_uint64),
-                ("reserved", ctypes.c_uint64 * 6)]
+                ("evals_first_pass", ctypes.c_uint64), ("rays_first_pass", ctypes.c_uint64),
+                ("reserved", ctypes.c_uint64 * 4)]
 
     def as_dict(self) -> dict:
         return {f: int(getattr(self, f)) for f, _ in self._fields_ if f != "reserved"}
@@ -116,6 +117,8 @@ def library():
     lib.vor_batch_workspace_bytes.restype = i64
     lib.vor_build_batch_async.argtypes = [P, P, P, ctypes.c_int32, P, P, P, P, i64, P, P, P]
     lib.vor_build_batch_async.restype = i32
+    lib.vor_kernel_launches.argtypes = []
+    lib.vor_kernel_launches.restype = i64
     lib.vor_strerror.argtypes = [i32]
     lib.vor_strerror.restype = ctypes.c_char_p
     _lib = lib
@@ -174,6 +177,10 @@ def vor_host_scratch_bytes(n: int) -> int:
     return int(library().vor_host_scratch_bytes(int(n)))
 
 
+def vor_kernel_launches() -> int:
+    return int(library().vor_kernel_launches())
+
+
 def vor_strerror(code: int) -> str:
     try:
         return library().vor_strerror(int(code)).decode()
@@ -185,10 +192,14 @@ def vor_stage_timing(enable: bool) -> int:
     return int(library().vor_stage_timing(1 if enable else 0))
 
 
+STAGES = ("bucketing", "gather_first_pass", "projector_first_pass", "second_pass",
+          "large_cells", "compaction")
+
+
 def vor_stage_ms() -> list[float]:
-    """Device ms of [bucketing, pass 1, pass 2, large cells, compaction] of the last build."""
-    buf = (ctypes.c_float * 5)()
-    k = int(library().vor_stage_ms(buf, 5))
+    """Device ms of the stages (see STAGES) of the last timed build."""
+    buf = (ctypes.c_float * len(STAGES))()
+    k = int(library().vor_stage_ms(buf, len(STAGES)))
     if k < 0:
         raise VorError(k, "vor_stage_ms")
     return [float(buf[i]) for i in range(k)]

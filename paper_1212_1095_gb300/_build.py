@@ -43,6 +43,17 @@ def _fingerprint() -> str:
     return h.hexdigest()
 
 
+def kernel_fingerprint(names) -> str:
+    """Hash of the named csrc files and the compile flags: identifies the code
+    of one kernel (its translation unit and the headers it includes)."""
+    h = hashlib.sha256()
+    for name in sorted(names):
+        with open(os.path.join(CSRC, name), "rb") as f:
+            h.update(name.encode() + f.read())
+    h.update(" ".join(ARCH + FLAGS).encode())
+    return h.hexdigest()
+
+
 def build_library(force: bool = False, verbose: bool = False) -> str:
     """Build libvor.so if the sources changed since the last build."""
     os.makedirs(BUILD, exist_ok=True)

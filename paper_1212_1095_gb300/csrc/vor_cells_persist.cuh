@@ -430,6 +430,10 @@ __global__ void __launch_bounds__(NT) cells_persist_kernel(CellParams P, GatherO
             atomicAdd(&st[STAT_CANDIDATES], v[7]);
             atomicAdd(&st[STAT_WIDEN], v[8]);
             atomicMax(&st[STAT_MAXE], v[9]);
+            if (!P.cell_list) {                 // first pass: its own share of the work
+                atomicAdd(&st[STAT_EVALS1], v[2]);
+                atomicAdd(&st[STAT_RAYS1], v[0]);
+            }
         }
     }
 }

@@ -3,16 +3,30 @@
 
 namespace vor {
 
-template <int CMAX>
-static cudaError_t launch_pass(const CellParams &P, const GatherOut &G, float target, cudaStream_t st) {
+static GatherOut gather_out(const CellParams &P, int pass, int *gcount, long long *grho2, int *gpos) {
+    // both passes share one position buffer of n * (P1_CMAX - 4) entries; the
+    // second pass lists fewer cells (the deferred ones) with more sites each
+    const long long entries = (long long)P.n * (P1_CMAX - 4);
+    if (pass == 1) return GatherOut{gcount, grho2, gpos, P1_CMAX - 4, P.n};
+    return GatherOut{gcount, grho2, gpos, P2_CMAX - 4, (int)(entries / (P2_CMAX - 4))};
+}
+
+cudaError_t launch_gather_pass(const CellParams &P, int pass, int *gcount, long long *grho2, int *gpos,
+                               cudaStream_t st) {
     const int total_max = P.cell_list ? P.n_list : P.n;
-    gather_kernel<<<(total_max + 255) / 256, 256, 0, st>>>(P, G, target);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    const float target = pass == 1 ? (float)P.target : 2.2f * (float)P.target;
+    gather_kernel<<<(total_max + 255) / 256, 256, 0, st>>>(P, gather_out(P, pass, gcount, grho2, gpos),
+                                                          target);
+    return cudaGetLastError();
+}
+
+template <int CMAX>
+static cudaError_t launch_persist(const CellParams &P, const GatherOut &G, cudaStream_t st) {
+    const int total_max = P.cell_list ? P.n_list : P.n;
     auto kern = cells_persist_kernel<P_NT, CMAX, P_SMAX, P_EMAX, P_RMAX>;
     const int smem = P_NT * CMAX * (int)sizeof(float4);
     int resident = 0;
-    e = resident_grid((const void *)kern, P_NT, smem, resident);
+    cudaError_t e = resident_grid((const void *)kern, P_NT, smem, resident);
     if (e != cudaSuccess) return e;
     long long want = ((long long)total_max + P_NT - 1) / P_NT;
     long long grid = resident;
@@ -24,15 +38,8 @@ static cudaError_t launch_pass(const CellParams &P, const GatherOut &G, float ta
 
 cudaError_t launch_cells_pass(const CellParams &P, int pass, int *gcount, long long *grho2, int *gpos,
                               cudaStream_t st) {
-    // both passes share one position buffer of n * (P1_CMAX - 4) entries; the
-    // second pass lists fewer cells (the deferred ones) with more sites each
-    const long long entries = (long long)P.n * (P1_CMAX - 4);
-    if (pass == 1) {
-        GatherOut G{gcount, grho2, gpos, P1_CMAX - 4, P.n};
-        return launch_pass<P1_CMAX>(P, G, (float)P.target, st);
-    }
-    GatherOut G{gcount, grho2, gpos, P2_CMAX - 4, (int)(entries / (P2_CMAX - 4))};
-    return launch_pass<P2_CMAX>(P, G, 2.2f * (float)P.target, st);
+    const GatherOut G = gather_out(P, pass, gcount, grho2, gpos);
+    return pass == 1 ? launch_persist<P1_CMAX>(P, G, st) : launch_persist<P2_CMAX>(P, G, st);
 }
 
 int pass_gather_width() { return P1_CMAX - 4; }

@@ -22,7 +22,7 @@ enum : unsigned {
 // per-build counters (vor_stats order)
 enum {
     STAT_RAYS = 0, STAT_VTESTS, STAT_EVALS, STAT_EXACT, STAT_ANNULUS, STAT_RERUNS,
-    STAT_DEFERRED, STAT_CANDIDATES, STAT_MAXE, STAT_WIDEN, STAT_N = 16
+    STAT_DEFERRED, STAT_CANDIDATES, STAT_MAXE, STAT_WIDEN, STAT_EVALS1, STAT_RAYS1, STAT_N = 16
 };
 
 // Workspace header (first 256 bytes of the workspace).
@@ -144,7 +144,10 @@ cudaError_t resident_grid(const void *kern, int threads, int smem, int &grid);
 
 // Launchers (vor_cells.cu)
 cudaError_t launch_cells_fast(const CellParams &P, int lanes, cudaStream_t st);
-// one thread per cell; pass 1 over all cells, pass 2 over the list P.cell_list
+// one thread per cell; pass 1 over all cells, pass 2 over the list
+// P.cell_list: first the candidate gather, then the persistent projector
+cudaError_t launch_gather_pass(const CellParams &P, int pass, int *gcount, long long *grho2, int *gpos,
+                               cudaStream_t st);
 cudaError_t launch_cells_pass(const CellParams &P, int pass, int *gcount, long long *grho2, int *gpos,
                               cudaStream_t st);
 int pass_gather_width();

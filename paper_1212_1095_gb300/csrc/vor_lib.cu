@@ -19,6 +19,7 @@
 //                      Delaunay pairs (Section 6), labels local to the set
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 #include <cuda_runtime.h>
 
@@ -550,15 +551,19 @@ static bool resolve(const int64_t *set_ptr, const vor_box *boxes, int n_sets, in
     return true;
 }
 
-// stage timing (vor_stage_timing / vor_stage_ms)
+// stage timing (vor_stage_timing / vor_stage_ms): events 0..N_STAGES
+constexpr int N_STAGES = 6;
 static bool g_timing = false;
-static cudaEvent_t g_ev[6];
+static cudaEvent_t g_ev[N_STAGES + 1];
 static bool g_ev_made = false;
 static bool g_ev_recorded = false;
 
 static void mark(int i, cudaStream_t st) {
     if (g_timing) cudaEventRecord(g_ev[i], st);
 }
+
+// kernels launched by this library in this process (vor_kernel_launches)
+static std::atomic<long long> g_launches{0};
 
 struct BatchArgs {
     const int2 *sites;
@@ -595,10 +600,16 @@ static int launch_build(const BatchArgs &A, const vor_opts *o, void *ws, const L
     int *coarse = (int *)(base + L.coarse);
     const int2 *sites = A.sites;
 
+    long long launched = 0;
+    struct Count {                    // adds this build's launches to the total
+        long long &n;
+        ~Count() { g_launches += n; }
+    } count_on_exit{launched};
     mark(0, st);
     if (cudaMemsetAsync(hdr, 0, 256, st) != cudaSuccess) return VOR_E_CUDA;
     k_plan<<<1, SCAN_T, 0, st>>>(A.set_ptr, A.boxes, L.n_sets, A.n1, A.box1, L.s_fixed, L.n,
                                  L.m_sum, L.g_sum, sets, hdr);
+    launched++;
     if (n == 0) {
         // nothing but empty sets: empty outputs
         if (cudaMemsetAsync(out->cell_ptr, 0, 8, st) != cudaSuccess ||
@@ -606,24 +617,32 @@ static int launch_build(const BatchArgs &A, const vor_opts *o, void *ws, const L
             (A.del_set_ptr &&
              cudaMemsetAsync(A.del_set_ptr, 0, (size_t)(L.n_sets + 1) * 8, st) != cudaSuccess))
             return VOR_E_CUDA;
-        for (int i = 1; i < 6; i++) mark(i, st);
+        for (int i = 1; i <= N_STAGES; i++) mark(i, st);
         if (g_timing) g_ev_recorded = true;
         return cudaGetLastError() == cudaSuccess ? VOR_OK : VOR_E_CUDA;
     }
     if (cudaMemsetAsync(bstart, 0, (size_t)(L.m_sum + 1) * 4, st) != cudaSuccess) return VOR_E_CUDA;
     const int T = 256;
     const int gn = (n + T - 1) / T;
-    if (sset) k_site_set<<<gn, T, 0, st>>>(A.set_ptr, L.n_sets, n, sset, hdr);
+    if (sset) {
+        k_site_set<<<gn, T, 0, st>>>(A.set_ptr, L.n_sets, n, sset, hdr);
+        launched++;
+    }
     if (L.s_fixed <= 0) {
         if (cudaMemsetAsync(coarse, 0, (size_t)L.g_sum * 4, st) != cudaSuccess) return VOR_E_CUDA;
         k_probe_count<<<gn, T, 0, st>>>(sites, n, sets, sset, coarse, hdr);
         k_probe_mean<<<gn, T, 0, st>>>(sites, n, sets, sset, coarse, hdr);
+        launched += 2;
     }
     k_pick_grid<<<1, SCAN_T, 0, st>>>(sets, L.n_sets, L.s_fixed, hdr);
     k_bucket_count<<<gn, T, 0, st>>>(sites, n, sets, sset, bstart, rank, hdr);
     scan<int>(bstart, (int)L.m_sum, &hdr->m_total, bstart, (int *)partial, nullptr, hdr, st);
     k_bucket_scatter<<<gn, T, 0, st>>>(sites, n, sets, sset, bstart, rank, sxy, sid, hdr);
-    if (o->check_duplicates) k_dup_check<<<gn, T, 0, st>>>(sxy, n, sets, sset, bstart, hdr);
+    launched += 6;                    // pick, count, 3 scan kernels, scatter
+    if (o->check_duplicates) {
+        k_dup_check<<<gn, T, 0, st>>>(sxy, n, sets, sset, bstart, hdr);
+        launched++;
+    }
     if (cudaGetLastError() != cudaSuccess) return VOR_E_CUDA;
     mark(1, st);
 
@@ -644,8 +663,10 @@ static int launch_build(const BatchArgs &A, const vor_opts *o, void *ws, const L
         // (or that exceed its table) go on to the second pass
         P.deferred = deferred;
         P.deferred_count = &hdr->ndeferred;
-        if (launch_cells_pass(P, 1, gcount, grho2, gpos, st) != cudaSuccess) return VOR_E_CUDA;
+        if (launch_gather_pass(P, 1, gcount, grho2, gpos, st) != cudaSuccess) return VOR_E_CUDA;
         mark(2, st);
+        if (launch_cells_pass(P, 1, gcount, grho2, gpos, st) != cudaSuccess) return VOR_E_CUDA;
+        mark(3, st);
         // second pass: a disc with about 2.2 times the sites
         CellParams P2 = P;
         P2.cell_list = deferred;
@@ -653,14 +674,18 @@ static int launch_build(const BatchArgs &A, const vor_opts *o, void *ws, const L
         P2.n_list = n;
         P2.deferred = deferred2;
         P2.deferred_count = &hdr->ndeferred2;
+        if (launch_gather_pass(P2, 2, gcount, grho2, gpos, st) != cudaSuccess) return VOR_E_CUDA;
         if (launch_cells_pass(P2, 2, gcount, grho2, gpos, st) != cudaSuccess) return VOR_E_CUDA;
-        mark(3, st);
+        launched += 4;                // two gathers, two persistent passes
+        mark(4, st);
     } else {
         P.deferred = deferred2;
         P.deferred_count = &hdr->ndeferred2;
-        if (launch_cells_fast(P, L.lanes, st) != cudaSuccess) return VOR_E_CUDA;
         mark(2, st);
+        if (launch_cells_fast(P, L.lanes, st) != cudaSuccess) return VOR_E_CUDA;
+        launched++;
         mark(3, st);
+        mark(4, st);
     }
     // warp per cell, large capacities, for what is left
     CellParams PL = P;
@@ -670,7 +695,8 @@ static int launch_build(const BatchArgs &A, const vor_opts *o, void *ws, const L
     PL.deferred = nullptr;
     PL.deferred_count = nullptr;
     if (launch_cells_large(PL, n, st) != cudaSuccess) return VOR_E_CUDA;
-    mark(4, st);
+    launched++;
+    mark(5, st);
 
     scan<long long>(ecount, n, nullptr, (long long *)out->cell_ptr, partial, (long long *)out->totals,
                     hdr, st);
@@ -682,11 +708,14 @@ static int launch_build(const BatchArgs &A, const vor_opts *o, void *ws, const L
     Q.edge_label = out->edge_label; Q.vx = out->vx; Q.vy = out->vy; Q.del_edge = out->del_edge;
     Q.edge_cap = out->edge_cap; Q.del_cap = out->del_cap; Q.hdr = hdr;
     k_compact<<<gn, T, 0, st>>>(Q);
-    if (A.del_set_ptr)
+    launched += 7;                    // 2 x 3 scan kernels, compaction
+    if (A.del_set_ptr) {
         k_set_del_ptr<<<(L.n_sets + 1 + T - 1) / T, T, 0, st>>>(sets, L.n_sets, n, del_ptr,
                                                                  A.del_set_ptr, hdr);
+        launched++;
+    }
     if (cudaGetLastError() != cudaSuccess) return VOR_E_CUDA;
-    mark(5, st);
+    mark(N_STAGES, st);
     if (g_timing) g_ev_recorded = true;
     return VOR_OK;
 }
@@ -825,6 +854,8 @@ int vor_status(const void *d_workspace, void *stream, vor_stats *stats) {
         stats->candidates = h.stats[STAT_CANDIDATES];
         stats->max_edges = h.stats[STAT_MAXE];
         stats->widenings = h.stats[STAT_WIDEN];
+        stats->evals_first_pass = h.stats[STAT_EVALS1];
+        stats->rays_first_pass = h.stats[STAT_RAYS1];
     }
     return map_err(h.err);
 }
@@ -937,7 +968,7 @@ int vor_build_host(const vor_site *h_sites, int64_t n, vor_box box, const vor_op
 
 int vor_stage_timing(int enable) {
     if (enable && !g_ev_made) {
-        for (int i = 0; i < 6; i++)
+        for (int i = 0; i <= N_STAGES; i++)
             if (cudaEventCreate(&g_ev[i]) != cudaSuccess) return VOR_E_CUDA;
         g_ev_made = true;
     }
@@ -949,12 +980,14 @@ int vor_stage_timing(int enable) {
 int vor_stage_ms(float *ms, int max_stages) {
     if (!ms || max_stages < 1) return VOR_E_INVALID_ARG;
     if (!g_ev_made || !g_ev_recorded) return VOR_E_INVALID_ARG;
-    if (cudaEventSynchronize(g_ev[5]) != cudaSuccess) return VOR_E_CUDA;
+    if (cudaEventSynchronize(g_ev[N_STAGES]) != cudaSuccess) return VOR_E_CUDA;
     int k = 0;
-    for (int i = 0; i < 5 && k < max_stages; i++, k++)
+    for (int i = 0; i < N_STAGES && k < max_stages; i++, k++)
         if (cudaEventElapsedTime(&ms[i], g_ev[i], g_ev[i + 1]) != cudaSuccess) return VOR_E_CUDA;
     return k;
 }
+
+int64_t vor_kernel_launches(void) { return (int64_t)g_launches.load(); }
 
 const char *vor_strerror(int code) {
     switch (code) {
