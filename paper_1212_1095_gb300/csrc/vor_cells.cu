@@ -18,15 +18,21 @@ cudaError_t launch_cells_fast(const CellParams &P, int lanes, cudaStream_t st) {
     }
 }
 
-cudaError_t launch_cells_large(const CellParams &P, int max_cells, cudaStream_t st) {
-    auto kern = cells_kernel<32, L_CMAX, L_SMAX, L_EMAX, L_RMAX, true>;
-    const int smem = (int)sizeof(LargeSmem);
+template <int CMAX, int SMAX, int EMAX, int RMAX>
+static cudaError_t launch_tier(const CellParams &P, int max_cells, cudaStream_t st) {
+    auto kern = cells_kernel<32, CMAX, SMAX, EMAX, RMAX, true>;
+    const int smem = (int)sizeof(GroupSmem<CMAX, SMAX, EMAX>);
     int grid = 0;
     cudaError_t e = resident_grid((const void *)kern, 32, smem, grid);
     if (e != cudaSuccess) return e;
     if (max_cells < grid) grid = max_cells > 0 ? max_cells : 1;
     kern<<<grid, 32, smem, st>>>(P);
     return cudaGetLastError();
+}
+
+cudaError_t launch_cells_large(const CellParams &P, int tier, int max_cells, cudaStream_t st) {
+    if (tier == 0) return launch_tier<M_CMAX, M_SMAX, M_EMAX, M_RMAX>(P, max_cells, st);
+    return launch_tier<L_CMAX, L_SMAX, L_EMAX, L_RMAX>(P, max_cells, st);
 }
 
 }  // namespace vor

@@ -52,7 +52,8 @@ struct __align__(16) GroupSmem {
     short scw[SMAX], sccw[SMAX]; // their clockwise / counter-clockwise lines
     short emit[EMAX];            // edges, counter-clockwise
     float vx[EMAX], vy[EMAX];    // approximate vertices relative to p
-    short vord[EMAX];            // vertices by distance from p (large-cell certificate)
+    float vr[EMAX];              // |v - p|, padded (vertex-disc radii of the certificate)
+    short tmp[EMAX];             // scratch of the candidate compaction
     int ncand;                   // candidate count while appending
     int flag;
 };
@@ -344,66 +345,147 @@ __device__ int projector(GroupSmem<CMAX, SMAX, EMAX> &S, const int C, const int 
     return ne;
 }
 
-// Append to the candidates the sites a != p with r2lo < |a - p|^2 <= r2hi
-// (all of them, or with cut_only those that cut the polygon S.vx/S.vy of e
-// vertices), scanning the buckets that meet the square of half-side
-// sqrt(r2hi) around p.  Uses S.ncand as the append counter and sets S.flag
-// when the table would grow past cap.  Returns the number of sites examined
-// (for the work budget).
-template <int G, int CMAX, int SMAX, int EMAX>
-__device__ int scan_disc(const CellParams &P, const CellGrid &g, GroupSmem<CMAX, SMAX, EMAX> &S,
-                         const int2 p, const int self, const i64 r2lo, const i64 r2hi,
-                         const bool cut_only, const int e, const int cap, const int gl, Counters &cnt) {
-    const int s = g.s;
-    const int r = (int)ceilf(sqrtf((float)r2hi)) + 1;
-    const int bx0 = p.x - r <= 0 ? 0 : (p.x - r) / s;
-    const int bx1 = min(g.m1 - 1, (p.x + r) / s);
-    const int by0 = p.y - r <= 0 ? 0 : (p.y - r) / s;
-    const int by1 = min(g.m2 - 1, (p.y + r) / s);
+// Walk the sites of the bucket rows by0..by1 with the G lanes of a group.
+// row_span(row, x0, x1) names the buckets of a row to visit (false: none).
+// Each lane reads the site range of one row; a prefix sum of the range
+// lengths over the group then lets the lanes take consecutive sites of the
+// concatenated ranges, so rows of unequal length keep every lane busy and
+// the rows' offset loads overlap instead of following one another.
+// visit(pos) runs once per site position.  Returns the sites visited.
+template <int G, class RowSpan, class Visit>
+__device__ __forceinline__ int scan_rows(const CellGrid &g, int by0, int by1, int gl, unsigned gmask,
+                                         RowSpan row_span, Visit visit) {
     int seen = 0;
-    for (int row = by0; row <= by1; row++) {
-        const int a = g.bs[row * g.m1 + bx0], b = g.bs[row * g.m1 + bx1 + 1];
-        seen += b - a;
-        for (int pos = a + gl; pos < b; pos += G) {
-            if (pos == self) continue;
-            const int2 q = P.sxy[pos];
-            const int nx = q.x - p.x, ny = q.y - p.y;
-            const i64 cc = (i64)nx * nx + (i64)ny * ny;
-            if (cc <= r2lo || cc > r2hi) continue;
-            const float fnx = (float)nx, fny = (float)ny, fc = (float)cc;
-            if (cut_only) {
-                cnt.annulus++;
-                bool cut = false;
-                for (int v = 0; v < e && !cut; v++) {
-                    const float vx = S.vx[v], vy = S.vy[v];
-                    const float f = 2.f * fmaf(fnx, vx, fny * vy) - fc;
-                    const float mg = 0x1p-16f * (2.f * (fabsf(fnx * vx) + fabsf(fny * vy)) + fc);
-                    if (f > mg) cut = true;
-                    else if (f >= -mg) {
-                        const int la = S.emit[v], lb = S.emit[v + 1 < e ? v + 1 : 0];
-                        int n1x, n1y, n2x, n2y;
-                        i64 c1, c2, Nx, Ny, D;
-                        cand_int(S, la, n1x, n1y, c1);
-                        cand_int(S, lb, n2x, n2y, c2);
-                        intersect(n1x, n1y, c1, n2x, n2y, c2, Nx, Ny, D);
-                        const i128 lhs = 2 * dot128(nx, ny, Nx, Ny) * (i128)(D > 0 ? 1 : -1);
-                        const i128 rhs = (i128)cc * (D > 0 ? D : -D);
-                        if (lhs > rhs) cut = true;
-                    }
-                }
-                if (!cut) continue;
+    for (int r0 = by0; r0 <= by1; r0 += G) {
+        const int row = r0 + gl;
+        int a = 0, len = 0;
+        if (row <= by1) {
+            int x0 = 0, x1 = -1;
+            if (row_span(row, x0, x1) && x0 <= x1) {
+                const int *rb = g.bs + (size_t)row * g.m1;
+                a = rb[x0];
+                len = rb[x1 + 1] - a;
             }
-            const int at = atomicAdd(&S.ncand, 1);
-            if (at < cap) {
-                const float rc = 1.f / fc;
-                S.cand[at] = make_float4(fnx, fny, rc, (float)(abs(nx) + abs(ny)) * rc);
-                S.lab[at] = P.sid[pos] - g.site_base;
-            } else {
-                S.flag = 1;
+        }
+        int incl = len;
+#pragma unroll
+        for (int off = 1; off < G; off <<= 1) {
+            const int y = __shfl_up_sync(gmask, incl, off, G);
+            if (gl >= off) incl += y;
+        }
+        const int total = __shfl_sync(gmask, incl, G - 1, G);
+        const int excl = incl - len;
+        seen += total;
+        for (int k0 = 0; k0 < total; k0 += G) {
+            const int k = k0 + gl;
+            int j = 0;                       // the last lane whose range starts at or before k
+#pragma unroll
+            for (int step = G / 2; step > 0; step >>= 1) {
+                const int ex = __shfl_sync(gmask, excl, j + step, G);
+                if (ex <= k) j += step;
             }
+            const int aj = __shfl_sync(gmask, a, j, G);
+            const int ej = __shfl_sync(gmask, excl, j, G);
+            if (k < total) visit(aj + (k - ej));
         }
     }
     return seen;
+}
+
+// Buckets of a row (band [row s, row s + s] in y) that meet the disc of
+// squared radius r2 around (cx, cy): the chord's x-range, widened by one unit.
+__device__ __forceinline__ bool disc_row_span(const CellGrid &g, int row, int cx, int cy, i64 r2,
+                                              int &x0, int &x1) {
+    const i64 ylo = (i64)row * g.s, yhi = ylo + g.s;
+    const i64 dy = cy < ylo ? ylo - cy : (cy > yhi ? cy - yhi : 0);
+    if (dy * dy > r2) return false;
+    const float h = sqrtf((float)(r2 - dy * dy)) + 1.f;   // error < 0.25 + rounding
+    x0 = max(0, (int)floorf(((float)cx - h) / (float)g.s));
+    x1 = min(g.m1 - 1, (int)floorf(((float)cx + h) / (float)g.s));
+    return true;
+}
+
+// Does the site n = a - p (c = |n|^2) cut the polygon of e vertices in
+// S.vx/S.vy (relative to p)?  It does iff it lies strictly inside the disc
+// of some vertex v through p: 2 <n, v> > c.  Float filter with a bound,
+// exact (the vertex as N/D of its two lines) when the bound cannot decide.
+template <class SM>
+__device__ __forceinline__ bool cuts_polygon(const SM &S, int e, int nx, int ny, i64 cc) {
+    const float fnx = (float)nx, fny = (float)ny, fc = (float)cc;
+    for (int v = 0; v < e; v++) {
+        const float vx = S.vx[v], vy = S.vy[v];
+        const float f = 2.f * fmaf(fnx, vx, fny * vy) - fc;
+        const float mg = 0x1p-16f * (2.f * (fabsf(fnx * vx) + fabsf(fny * vy)) + fc);
+        if (f > mg) return true;
+        if (f >= -mg) {
+            const int la = S.emit[v], lb = S.emit[v + 1 < e ? v + 1 : 0];
+            int n1x, n1y, n2x, n2y;
+            i64 c1, c2, Nx, Ny, D;
+            cand_int(S, la, n1x, n1y, c1);
+            cand_int(S, lb, n2x, n2y, c2);
+            intersect(n1x, n1y, c1, n2x, n2y, c2, Nx, Ny, D);
+            const i128 lhs = 2 * dot128(nx, ny, Nx, Ny) * (i128)(D > 0 ? 1 : -1);
+            const i128 rhs = (i128)cc * (D > 0 ? D : -D);
+            if (lhs > rhs) return true;
+        }
+    }
+    return false;
+}
+
+// Append to the candidates the sites a != p with r2lo < |a - p|^2 <= r2hi:
+// all of them, or with cut_only those that cut the polygon S.vx/S.vy of e
+// vertices.  With flower, only the parts of the rows that meet some vertex
+// disc (S.vr radii) are read: a site outside every vertex disc cannot cut.
+// Uses S.ncand as the append counter and sets S.flag when the table would
+// grow past cap.  Returns the number of sites examined.
+template <int G, int CMAX, int SMAX, int EMAX>
+__device__ int scan_disc(const CellParams &P, const CellGrid &g, GroupSmem<CMAX, SMAX, EMAX> &S,
+                         const int2 p, const int self, const i64 r2lo, const i64 r2hi,
+                         const bool cut_only, const int e, const int cap, const int gl,
+                         const unsigned gmask, Counters &cnt, const bool flower = false) {
+    const int s = g.s;
+    const int r = (int)ceilf(sqrtf((float)r2hi)) + 1;
+    const int by0 = p.y - r <= 0 ? 0 : (p.y - r) / s;
+    const int by1 = min(g.m2 - 1, (p.y + r) / s);
+    auto span = [&](int row, int &x0, int &x1) -> bool {
+        if (!disc_row_span(g, row, p.x, p.y, r2hi, x0, x1)) return false;
+        if (!flower) return true;
+        // bounding x-range of the vertex-disc chords in this row
+        const float ylo = (float)row * (float)s, yhi = ylo + (float)s;
+        float ulo = FLT_MAX, uhi = -FLT_MAX;
+        for (int v = 0; v < e; v++) {
+            const float vxa = (float)p.x + S.vx[v], vya = (float)p.y + S.vy[v], rv = S.vr[v];
+            const float dv = fmaxf(0.f, fmaxf(ylo - vya, vya - yhi));
+            if (dv > rv) continue;
+            const float h = sqrtf(fmaxf(rv * rv - dv * dv, 0.f)) + 1.f;
+            ulo = fminf(ulo, vxa - h);
+            uhi = fmaxf(uhi, vxa + h);
+        }
+        if (ulo > uhi) return false;
+        x0 = max(x0, (int)floorf(fmaxf(ulo, -1.f) / (float)s));
+        x1 = min(x1, (int)floorf(fminf(uhi, (float)g.W + 1.f) / (float)s));
+        return true;
+    };
+    auto visit = [&](int pos) {
+        if (pos == self) return;
+        const int2 q = P.sxy[pos];
+        const int nx = q.x - p.x, ny = q.y - p.y;
+        const i64 cc = (i64)nx * nx + (i64)ny * ny;
+        if (cc <= r2lo || cc > r2hi) return;
+        if (cut_only) {
+            cnt.annulus++;
+            if (!cuts_polygon(S, e, nx, ny, cc)) return;
+        }
+        const int at = atomicAdd(&S.ncand, 1);
+        if (at < cap) {
+            const float fc = (float)cc, rc = 1.f / fc;
+            S.cand[at] = make_float4((float)nx, (float)ny, rc, (float)(abs(nx) + abs(ny)) * rc);
+            S.lab[at] = P.sid[pos] - g.site_base;
+        } else {
+            S.flag = 1;
+        }
+    };
+    return scan_rows<G>(g, by0, by1, gl, gmask, span, visit);
 }
 
 // vertices of the polygon (S.emit, e edges) into S.vx/S.vy; returns max |v-p|^2
@@ -423,155 +505,90 @@ __device__ float polygon_vertices(GroupSmem<CMAX, SMAX, EMAX> &S, const int e, c
         const float vx = (float)Nx * rd, vy = (float)Ny * rd;
         S.vx[q] = vx;
         S.vy[q] = vy;
-        R2 = fmaxf(R2, fmaf(vx, vx, vy * vy));
+        const float r2 = fmaf(vx, vx, vy * vy);
+        // disc radius padded for the float vertex: relative 2^-10 (far above the
+        // float error of v and of the chord computation r^2 - d^2) plus 2 units
+        S.vr[q] = sqrtf(r2) * (1.f + 0x1p-10f) + 2.f;
+        R2 = fmaxf(R2, r2);
     }
     return group_max<G>(R2, gmask);
 }
 
 
-// Site a (n = a - p, c = |n|^2) lies strictly inside the disc of vertex q of
-// the polygon (centre v, through p), i.e. cuts the polygon at v:
-// |a - v| < |p - v|  <=>  2 <n, v - p> > c.  Float filter, exact on doubt.
-template <class SM>
-__device__ __forceinline__ bool cuts_vertex(const SM &S, int e, int q, int nx, int ny, i64 cc) {
-    const float fnx = (float)nx, fny = (float)ny, fc = (float)cc;
-    const float vx = S.vx[q], vy = S.vy[q];
-    const float f = 2.f * fmaf(fnx, vx, fny * vy) - fc;
-    const float mg = 0x1p-16f * (2.f * (fabsf(fnx * vx) + fabsf(fny * vy)) + fc);
-    if (f > mg) return true;
-    if (f < -mg) return false;
-    int n1x, n1y, n2x, n2y;
-    i64 c1, c2, Nx, Ny, D;
-    cand_int(S, S.emit[q], n1x, n1y, c1);
-    cand_int(S, S.emit[q + 1 < e ? q + 1 : 0], n2x, n2y, c2);
-    intersect(n1x, n1y, c1, n2x, n2y, c2, Nx, Ny, D);
-    const i128 lhs = 2 * dot128(nx, ny, Nx, Ny) * (i128)(D > 0 ? 1 : -1);
-    return lhs > (i128)cc * (D > 0 ? D : -D);
-}
-
 // Large-cell certificate.  A site that is not a candidate can cut the
-// polygon only if it lies strictly inside the empty disc of some vertex v
-// (centre v, through p): the part of the polygon beyond a's bisector holds a
-// vertex v of the polygon with |a - v| < |p - v|.  Each round
-//   1. drops the candidates that carry no edge (their half-planes contain
-//      the polygon and every later, smaller polygon),
-//   2. scans, nearest vertex first, the sites inside both a vertex disc and
-//      the disc of radius rho around p (through the bucket rows both meet),
-//   3. adds the cutters found (as many as the table holds) and reruns the
-//      projector; with no cutter, rho doubles until it reaches 2R, where
-//      every vertex disc lies inside it and the polygon is the cell.
+// polygon only if it lies strictly inside the disc of some vertex v (centre
+// v, through p): the part of the polygon beyond the site's bisector holds a
+// vertex v with |a - v| < |p - v| (the "flower" of the polygon is the union
+// of these discs).  Invariant: every site within rho of p is a candidate or
+// cuts no polygon from here on (the polygons only shrink, and so do their
+// flowers).  Each round
+//   1. stops when 2R <= rho (no site beyond rho can cut, Lemmas Byy'Syy' and
+//      SitesInLargeSquare) or rho covers the whole box;
+//   2. keeps only the candidates that carry an edge (the half-planes of the
+//      others contain this polygon and every later one);
+//   3. scans the annulus rho < |a - p| <= rho' (rho' = min(2 rho, 2R)),
+//      reading only the parts of the bucket rows that meet the flower, and
+//      adds the sites that cut the polygon (if the table would overflow, a
+//      thinner annulus is scanned first);
+//   4. reruns the projector with them; then every site within rho' is a
+//      candidate or cuts no later polygon, and rho := rho'.
 template <int G, int CMAX, int SMAX, int EMAX, int RMAX>
 __device__ int certify_by_vertex_discs(const CellParams &P, const CellGrid &g,
                                        GroupSmem<CMAX, SMAX, EMAX> &S, const int2 p, const int i,
                                        i64 rho2, int &C, int &e, const int gl,
                                        const unsigned gmask, Counters &cnt) {
-    const int s = g.s, m1 = g.m1, m2 = g.m2;
     const i64 cxf = max(p.x, g.W - p.x), cyf = max(p.y, g.H - p.y);
     const i64 far2 = cxf * cxf + cyf * cyf;            // no site is farther than a corner
     for (int round = 0; round < 4096; round++) {
+        if (gl == 0) S.flag = 0;
+        group_sync<G>(gmask);
         const float R2 = polygon_vertices<G>(S, e, gl, gmask);
         group_sync<G>(gmask);
         if (S.flag == 2) return CELL_FAIL;
+        const i64 need = (i64)(4.f * (R2 * (1.f + 0x1p-12f) + 1.f)) + 1;   // > (2R)^2
+        if (need <= rho2 || rho2 >= far2) return CELL_OK;
         if (gl == 0) {
-            // 1. keep the edge lines only: entries in ascending old index,
-            //    then renumber the edge list
-            for (int q = 0; q < e; q++) S.vord[q] = S.emit[q];
+            // keep the edge lines only: entries in ascending old index, then
+            // renumber the edge list (vertex q stays between edges q, q+1)
+            for (int q = 0; q < e; q++) S.tmp[q] = S.emit[q];
             for (int x = 1; x < e; x++) {
-                const short key = S.vord[x];
+                const short key = S.tmp[x];
                 int y = x - 1;
-                while (y >= 0 && S.vord[y] > key) { S.vord[y + 1] = S.vord[y]; y--; }
-                S.vord[y + 1] = key;
+                while (y >= 0 && S.tmp[y] > key) { S.tmp[y + 1] = S.tmp[y]; y--; }
+                S.tmp[y + 1] = key;
             }
             for (int q = 0; q < e; q++) {
-                const int src = S.vord[q];
+                const int src = S.tmp[q];
                 if (src != q) { S.cand[q] = S.cand[src]; S.lab[q] = S.lab[src]; }
             }
             for (int q = 0; q < e; q++) {
                 int j = 0;
-                while (S.vord[j] != S.emit[q]) j++;
+                while (S.tmp[j] != S.emit[q]) j++;
                 S.emit[q] = (short)j;
             }
-            // vertices by increasing distance from p
-            for (int q = 0; q < e; q++) S.vord[q] = (short)q;
-            for (int x = 1; x < e; x++) {
-                const short key = S.vord[x];
-                const float kd = S.vx[key] * S.vx[key] + S.vy[key] * S.vy[key];
-                int y = x - 1;
-                while (y >= 0 && S.vx[S.vord[y]] * S.vx[S.vord[y]] + S.vy[S.vord[y]] * S.vy[S.vord[y]] > kd) {
-                    S.vord[y + 1] = S.vord[y];
-                    y--;
-                }
-                S.vord[y + 1] = key;
-            }
-            S.ncand = e;
-            S.flag = 0;
         }
         C = e;
-        group_sync<G>(gmask);
-        // 2. sites inside a vertex disc and within rho of p
-        const float rho = sqrtf((float)rho2) + 1.f;
-        for (int qi = 0; qi < e; qi++) {
-            const int q = S.vord[qi];
-            const float vx = (float)p.x + S.vx[q], vy = (float)p.y + S.vy[q];
-            const float r = sqrtf(S.vx[q] * S.vx[q] + S.vy[q] * S.vy[q]) * (1.f + 0x1p-10f) + 2.f;
-            const float ylo_all = fmaxf(vy - r, (float)p.y - rho), yhi_all = fminf(vy + r, (float)p.y + rho);
-            if (ylo_all > yhi_all) continue;
-            const int by0 = max(0, (int)floorf(ylo_all / (float)s));
-            const int by1 = min(m2 - 1, (int)floorf(yhi_all / (float)s));
-            for (int row = by0; row <= by1; row++) {
-                const float ylo = (float)row * (float)s, yhi = ylo + (float)s;
-                const float dv = fmaxf(0.f, fmaxf(ylo - vy, vy - yhi));
-                const float dp = fmaxf(0.f, fmaxf(ylo - (float)p.y, (float)p.y - yhi));
-                if (dv > r || dp > rho) continue;
-                const float hv = sqrtf(fmaxf(r * r - dv * dv, 0.f)) + 1.f;
-                const float hp = sqrtf(fmaxf(rho * rho - dp * dp, 0.f)) + 1.f;
-                const float xlo = fmaxf(vx - hv, (float)p.x - hp), xhi = fminf(vx + hv, (float)p.x + hp);
-                if (xlo > xhi) continue;
-                const int bx0 = max(0, (int)floorf(xlo / (float)s));
-                const int bx1 = min(m1 - 1, (int)floorf(xhi / (float)s));
-                if (bx0 > bx1) continue;
-                const int a = g.bs[row * m1 + bx0], b = g.bs[row * m1 + bx1 + 1];
-                for (int pos = a + gl; pos < b; pos += G) {
-                    if (pos == i) continue;
-                    const int2 site = P.sxy[pos];
-                    const int nx = site.x - p.x, ny = site.y - p.y;
-                    const i64 cc = (i64)nx * nx + (i64)ny * ny;
-                    if (cc > rho2) continue;
-                    cnt.annulus++;
-                    if (!cuts_vertex(S, e, q, nx, ny, cc)) continue;
-                    bool earlier = false;                  // found with a nearer vertex
-                    for (int qj = 0; qj < qi && !earlier; qj++)
-                        earlier = cuts_vertex(S, e, S.vord[qj], nx, ny, cc);
-                    if (earlier) continue;
-                    const int at = atomicAdd(&S.ncand, 1);
-                    if (at < CMAX) {
-                        const float fc = (float)cc, rc = 1.f / fc;
-                        S.cand[at] = make_float4((float)nx, (float)ny, rc, (float)(abs(nx) + abs(ny)) * rc);
-                        S.lab[at] = P.sid[pos] - g.site_base;
-                    } else {
-                        S.flag = 1;
-                    }
-                }
-            }
+        cnt.widen++;
+        i64 step2 = min(min(need, rho2 < ((i64)1 << 60) / 4 ? 4 * rho2 + 4 : rho2), far2);
+        for (int shrink = 0;; shrink++) {
+            if (gl == 0) { S.ncand = C; S.flag = 0; }
             group_sync<G>(gmask);
-            if (S.flag) break;                             // table full: use these first
+            scan_disc<G>(P, g, S, p, i, rho2, step2, true, e, CMAX, gl, gmask, cnt, true);
+            group_sync<G>(gmask);
+            if (!S.flag) break;
+            if (shrink >= 40 || step2 <= rho2 + 1) return CELL_DEFER;
+            step2 = rho2 + (step2 - rho2) / 4;             // too many cutters: a thinner annulus
         }
-        group_sync<G>(gmask);
-        const int ncut = min(S.ncand, CMAX) - e;
-        if (ncut == 0) {
-            // 3. no cutter within rho: certified once rho covers 2R
-            const i64 need = (i64)(4.f * (R2 * (1.f + 0x1p-12f) + 1.f)) + 1;
-            if (need <= rho2 || rho2 >= far2) return CELL_OK;
-            cnt.widen++;
-            rho2 = min(min(need, rho2 < ((i64)1 << 60) / 4 ? 4 * rho2 + 4 : rho2), far2);
-            continue;
+        rho2 = step2;
+        const int ncut = S.ncand - C;
+        if (ncut > 0) {
+            cnt.reruns++;
+            cnt.cands += ncut;
+            C += ncut;
+            e = projector<G, CMAX, SMAX, EMAX, RMAX>(S, C, gl, gmask, P.exact_only, cnt);
+            if (e < 0) return CELL_DEFER;
+            if (e < 3) return CELL_FAIL;
         }
-        cnt.reruns++;
-        cnt.cands += ncut;
-        C = e + ncut;
-        e = projector<G, CMAX, SMAX, EMAX, RMAX>(S, C, gl, gmask, P.exact_only, cnt);
-        if (e < 0) return CELL_DEFER;
-        if (e < 3) return CELL_FAIL;
     }
     return CELL_FAIL;
 }
@@ -613,7 +630,7 @@ __device__ int process_cell(const CellParams &P, GroupSmem<CMAX, SMAX, EMAX> &S,
     for (int attempt = 0;; attempt++) {
         if (gl == 0) { S.ncand = 0; S.flag = 0; }
         group_sync<G>(gmask);
-        scanned += scan_disc<G>(P, g, S, p, i, -1, rho2, false, 0, CMAX - 4, gl, cnt);
+        scanned += scan_disc<G>(P, g, S, p, i, -1, rho2, false, 0, CMAX - 4, gl, gmask, cnt);
         group_sync<G>(gmask);
         if (!S.flag) break;
         if (!LARGE || attempt >= 24 || rho2 <= 4) return CELL_DEFER;
@@ -668,7 +685,7 @@ __device__ int process_cell(const CellParams &P, GroupSmem<CMAX, SMAX, EMAX> &S,
         for (int shrink = 0;; shrink++) {
             if (gl == 0) { S.ncand = C; S.flag = 0; }
             group_sync<G>(gmask);
-            scanned += scan_disc<G>(P, g, S, p, i, rho2, step2, true, e, CMAX, gl, cnt);
+            scanned += scan_disc<G>(P, g, S, p, i, rho2, step2, true, e, CMAX, gl, gmask, cnt);
             group_sync<G>(gmask);
             if (!S.flag) break;
             // too many sites cut the polygon at once: test a thinner annulus
@@ -748,7 +765,7 @@ __global__ void cells_kernel(CellParams P) {
     int t = LARGE ? 0 : blockIdx.x * gpb + gib;
     for (;;) {
         if (LARGE) {
-            if (gl == 0) t = atomicAdd(&P.hdr->large_next, 1);
+            if (gl == 0) t = atomicAdd(P.next_cell, 1);
             t = __shfl_sync(gmask, t, 0, G);
         }
         if (t >= total) break;
@@ -784,10 +801,14 @@ __global__ void cells_kernel(CellParams P) {
 // ---- configurations ----------------------------------------------------------
 // first pass: 16 groups per block, small capacities, bounded certificate work
 constexpr int F_CMAX = 48, F_SMAX = 20, F_EMAX = 40, F_RMAX = 40, F_GROUPS = 16;
-// large-cell pass: one warp per cell, one cell per block
+// large-cell passes: one warp per cell, one cell per block; the medium tier
+// (about 7 KB of shared memory per warp) takes the deferred cells first and
+// hands the ones that exceed it to the large tier
+constexpr int M_CMAX = 256, M_SMAX = 64, M_EMAX = 64, M_RMAX = 256;
 constexpr int L_CMAX = 1024, L_SMAX = 256, L_EMAX = 256, L_RMAX = 1024;
 
 using FastSmem = GroupSmem<F_CMAX, F_SMAX, F_EMAX>;
+using MediumSmem = GroupSmem<M_CMAX, M_SMAX, M_EMAX>;
 using LargeSmem = GroupSmem<L_CMAX, L_SMAX, L_EMAX>;
 
 template <int G>

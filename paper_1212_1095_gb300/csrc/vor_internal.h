@@ -32,9 +32,11 @@ struct WsHeader {
     int ndeferred;          // cells handed from the first to the second pass
     int ndeferred2;         // cells handed to the warp-per-cell pass
     unsigned long long stats[STAT_N];
-    int large_next;         // next cell of the large-cell pass (dynamic schedule)
+    int large_next;         // next cell of the medium-cell pass (dynamic schedule)
     int m_total;            // buckets over all sets (set by the grid choice)
-    long long pad[11];
+    int ndeferred3;         // cells handed from the medium to the large tier
+    int large_next2;        // next cell of the large tier
+    long long pad[10];
 };
 static_assert(sizeof(WsHeader) <= 256, "header");
 
@@ -120,6 +122,7 @@ struct CellParams {
     int n_list;             // host upper bound of the list length (grid sizing)
     int *deferred;          // cells handed to the next pass
     int *deferred_count;    // device counter of that list
+    int *next_cell;         // dynamic schedule: next list entry to take (null: stride)
     WsHeader *hdr;
 };
 
@@ -151,7 +154,9 @@ cudaError_t launch_gather_pass(const CellParams &P, int pass, int *gcount, long 
 cudaError_t launch_cells_pass(const CellParams &P, int pass, int *gcount, long long *grho2, int *gpos,
                               cudaStream_t st);
 int pass_gather_width();
-cudaError_t launch_cells_large(const CellParams &P, int max_cells, cudaStream_t st);
+// one warp per cell over P.cell_list, cells taken from *P.next_cell; tier 0:
+// medium capacities (defers to P.deferred), tier 1: large capacities
+cudaError_t launch_cells_large(const CellParams &P, int tier, int max_cells, cudaStream_t st);
 int cells_fast_max_smem();
 int cells_large_capacity();
 

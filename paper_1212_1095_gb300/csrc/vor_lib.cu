@@ -480,7 +480,7 @@ struct Layout {
     int s_fixed, lanes, target, n_sets;
     long long n, m_sum, g_sum;
     size_t hdr, sets, sset, bstart, rank, sxy, sid, partial, ecount, dcount, loc, del_ptr, slot,
-        spill, deferred, deferred2, gcount, grho2, gpos, coarse, total;
+        spill, deferred, deferred2, deferred3, gcount, grho2, gpos, coarse, total;
     int spill_cap;
     int n_partial;
 };
@@ -543,6 +543,7 @@ static bool resolve(const int64_t *set_ptr, const vor_box *boxes, int n_sets, in
     L.spill = at;    at = align256(at + (size_t)L.spill_cap * 4);
     L.deferred = at; at = align256(at + nn * 4);
     L.deferred2 = at; at = align256(at + nn * 4);
+    L.deferred3 = at; at = align256(at + nn * 4);
     L.gcount = at;   at = align256(at + nn * 4);
     L.grho2 = at;    at = align256(at + nn * 8);
     L.gpos = at;     at = align256(at + nn * 4 * (size_t)pass_gather_width());
@@ -597,6 +598,7 @@ static int launch_build(const BatchArgs &A, const vor_opts *o, void *ws, const L
     int *spill = (int *)(base + L.spill);
     int *deferred = (int *)(base + L.deferred);
     int *deferred2 = (int *)(base + L.deferred2);
+    int *deferred3 = (int *)(base + L.deferred3);
     int *coarse = (int *)(base + L.coarse);
     const int2 *sites = A.sites;
 
@@ -687,15 +689,23 @@ static int launch_build(const BatchArgs &A, const vor_opts *o, void *ws, const L
         mark(3, st);
         mark(4, st);
     }
-    // warp per cell, large capacities, for what is left
-    CellParams PL = P;
-    PL.cell_list = deferred2;
-    PL.list_count = &hdr->ndeferred2;
-    PL.n_list = n;
+    // warp per cell for what is left: medium capacities, then large
+    CellParams PM = P;
+    PM.cell_list = deferred2;
+    PM.list_count = &hdr->ndeferred2;
+    PM.n_list = n;
+    PM.deferred = deferred3;
+    PM.deferred_count = &hdr->ndeferred3;
+    PM.next_cell = &hdr->large_next;
+    if (launch_cells_large(PM, 0, n, st) != cudaSuccess) return VOR_E_CUDA;
+    CellParams PL = PM;
+    PL.cell_list = deferred3;
+    PL.list_count = &hdr->ndeferred3;
     PL.deferred = nullptr;
     PL.deferred_count = nullptr;
-    if (launch_cells_large(PL, n, st) != cudaSuccess) return VOR_E_CUDA;
-    launched++;
+    PL.next_cell = &hdr->large_next2;
+    if (launch_cells_large(PL, 1, n, st) != cudaSuccess) return VOR_E_CUDA;
+    launched += 2;
     mark(5, st);
 
     scan<long long>(ecount, n, nullptr, (long long *)out->cell_ptr, partial, (long long *)out->totals,

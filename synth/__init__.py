@@ -326,3 +326,21 @@ def workload(name: str, cache: bool = True) -> np.ndarray:
         np.save(tmp, xy)
         os.replace(tmp, path)
     return xy
+
+
+def batch_workload(cache: bool = True):
+    """The batched workload: 4,096 sets of log-uniform size in [16, 65,536],
+    even sets uniform, odd sets Gaussian mixtures, all in [0, 2^20]^2.
+    Returns (sites int32[N,2], set_ptr int64[4097])."""
+    import os
+    seed = SEED_BASE + 4
+    path = os.path.join(_cache_dir(), f"batch_4096_{seed}.npz") if cache else None
+    if path and os.path.exists(path):
+        d = np.load(path)
+        return d["xy"], d["ptr"]
+    xy, ptr = batch_sets(n_sets=4096, seed=seed)
+    if path:
+        tmp = path + f".{os.getpid()}.npz"
+        np.savez(tmp, xy=xy, ptr=ptr)
+        os.replace(tmp, path)
+    return xy, ptr
