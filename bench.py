@@ -33,7 +33,7 @@ if ROOT not in sys.path:
 
 METRIC = "cells/s at n=1M uniform; batched sets/s and p50/p99 latency vs plain"
 BOX = 1 << 20
-WORKLOADS = {"uniform_1m": 1 << 20, "gauss_4m": 1 << 22}
+WORKLOADS = {"uniform_1m": 1 << 20, "gauss_4m": 1 << 22, "batch_4096": None, "serve": None}
 OPS_PER_EVAL = 8                # FP32/ALU operations of one filter evaluation of a candidate
 
 
@@ -49,6 +49,11 @@ def parse():
     ap.add_argument("--bucket-side", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="leave the batched sets/s and latency block out of the default line")
+    ap.add_argument("--batch-steps", type=int, default=5)
+    ap.add_argument("--requests", type=int, default=2000,
+                    help="serving: requests per measured stream")
     return ap.parse_args()
 
 
@@ -224,6 +229,355 @@ def run_reference(args):
     return 0
 
 
+
+def _batch_inputs(dev):
+    import numpy as np
+    import torch
+    import synth
+    xy, ptr = synth.batch_workload()
+    boxes = np.full((ptr.shape[0] - 1, 2), BOX, np.int32)
+    return xy, ptr, boxes, torch.from_numpy(xy).to(dev)
+
+
+def _sub_batch(xy, ptr, sel, dev):
+    """The sets sel of a batch as a batch of their own (autotuning sample)."""
+    import numpy as np
+    import torch
+    parts = [xy[ptr[j]:ptr[j + 1]] for j in sel]
+    sp = np.zeros(len(sel) + 1, np.int64)
+    sp[1:] = np.cumsum([p.shape[0] for p in parts])
+    return torch.from_numpy(np.concatenate(parts)).to(dev), sp, np.full((len(sel), 2), BOX, np.int32)
+
+
+def batch_measure(args, dev, steps: int, warmup: int, ws_n: int = 1) -> dict:
+    """Batched workload: 4,096 sets (log-uniform sizes in [16, 65,536], half
+    uniform, half Gaussian mixture) built as one batch, one CUDA graph replay
+    per step, with the options the autotuner picks on a sample of the sets;
+    beside it the same sets built one launch sequence per set ("plain")."""
+    import numpy as np
+    import torch
+
+    import paper_1212_1095_gb300 as vg
+
+    xy, ptr, boxes, d_sites = _batch_inputs(dev)
+    S, N = ptr.shape[0] - 1, int(ptr[-1])
+    stream = torch.cuda.current_stream()
+    # autotuning on every 7th set (an odd stride, so uniform and Gaussian
+    # sets alternate in the sample); the graph replays use the winner
+    fixed = args.lanes or args.target or args.bucket_side
+    t0 = time.perf_counter()
+    if fixed:
+        best = vg.vor_opts_default(lanes_per_cell=args.lanes, target=args.target,
+                                   bucket_side=args.bucket_side)
+        table = []
+    else:
+        d_s, sp, sb = _sub_batch(xy, ptr, np.arange(0, S, 7), dev)
+        best, table = vg.autotune_batch(d_s, sp, sb, reps=2)
+        del d_s
+    tune_s = time.perf_counter() - t0
+    # counters of one eager build, and the launches of one build
+    Wst = vg.BatchWorkspace(ptr, boxes, vg.vor_opts_default(collect_stats=1, **{
+        k: v for k, v in best.as_dict().items() if k in ("lanes_per_cell", "target",
+                                                          "bucket_side", "bucket_load_pct")}),
+        device=dev)
+    Wst.launch(d_sites)
+    Bst = Wst.finish()
+    stats = Bst.stats
+    n_edges, n_del = int(Wst.totals[0].item()), int(Wst.totals[1].item())
+    del Wst, Bst
+    torch.cuda.empty_cache()
+    W = vg.BatchWorkspace(ptr, boxes, best, device=dev)
+    vg.vor_stage_timing(True)
+    l0 = vg.vor_kernel_launches()
+    W.launch(d_sites)
+    W.finish()
+    per_build = vg.vor_kernel_launches() - l0
+    stages = vg.vor_stage_ms()
+    vg.vor_stage_timing(False)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        W.launch(d_sites)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(warmup):
+        g.replay()
+    torch.cuda.synchronize()
+    barrier(ws_n)
+    clocks = Clocks(int(dev.index or 0))
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    step_ms = []
+    for _ in range(steps):
+        flush.fill_(1)
+        e0.record(stream)
+        g.replay()
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    barrier(ws_n)
+    clk = clocks.stop()
+    rc, _ = vg.vor_status(W.ws_ptr, stream.cuda_stream)
+    if rc != 0:
+        raise vg.VorError(rc, "batched builds")
+    ms = statistics.mean(step_ms)
+    ms_max = max_over_ranks(ws_n, ms)
+
+    # end to end: pinned host sites -> device, graph replay, results -> pinned host
+    e2e = None
+    if not args.no_e2e:
+        h_sites = torch.from_numpy(xy).pin_memory()
+        h_cp = torch.empty(N + 1, dtype=torch.int64).pin_memory()
+        h_lab = torch.empty(n_edges, dtype=torch.int32).pin_memory()
+        h_vx = torch.empty(n_edges, dtype=torch.float64).pin_memory()
+        h_vy = torch.empty(n_edges, dtype=torch.float64).pin_memory()
+        h_dl = torch.empty((n_del, 2), dtype=torch.int32).pin_memory()
+        h_dsp = torch.empty(S + 1, dtype=torch.int64).pin_memory()
+
+        def e2e_step():
+            d_sites.copy_(h_sites, non_blocking=True)
+            g.replay()
+            h_cp.copy_(W.cell_ptr, non_blocking=True)
+            h_lab.copy_(W.labels[:n_edges], non_blocking=True)
+            h_vx.copy_(W.vx[:n_edges], non_blocking=True)
+            h_vy.copy_(W.vy[:n_edges], non_blocking=True)
+            h_dl.copy_(W.del_edge[:n_del], non_blocking=True)
+            h_dsp.copy_(W.del_set_ptr, non_blocking=True)
+            stream.synchronize()
+
+        e2e_step()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            e2e_step()
+        te = max_over_ranks(ws_n, (time.perf_counter() - t0) / steps)
+        e2e = {"value": ws_n * S / te, "unit": "sets/s", "h2d_bytes_per_step": 8 * N,
+               "d2h_bytes_per_step": 8 * (N + 1) + 20 * n_edges + 8 * n_del + 8 * (S + 1),
+               "ms_per_step": 1000.0 * te}
+    del g, W
+    torch.cuda.empty_cache()
+
+    # plain: each set built by its own launch sequence, one after another on
+    # the stream; a set's latency is the time from the first launch to its
+    # completion
+    sizes = np.diff(ptr)
+    nmax = int(sizes.max())
+    plain_opts = vg.vor_opts_default()                 # plain: default options, no graph
+    ws_b = max(vg.vor_workspace_bytes(int(n), BOX, plain_opts) for n in np.unique(sizes))
+    wsp = torch.empty(ws_b + 256, dtype=torch.uint8, device=dev)
+    wp = (wsp.data_ptr() + 255) & ~255
+    ec, dc = vg.vor_edge_capacity(nmax), vg.vor_delaunay_capacity(nmax)
+    bufs = [torch.empty(nmax + 1, dtype=torch.int64, device=dev),
+            torch.empty(ec, dtype=torch.int32, device=dev),
+            torch.empty(ec, dtype=torch.float64, device=dev),
+            torch.empty(ec, dtype=torch.float64, device=dev),
+            torch.empty(2 * dc, dtype=torch.int32, device=dev),
+            torch.empty(2, dtype=torch.int64, device=dev)]
+    out = vg.VorOut(*[b.data_ptr() for b in bufs], ec, dc)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(S + 1)]
+    base = d_sites.data_ptr()
+
+    def plain(record):
+        if record:
+            evs[0].record(stream)
+        for j in range(S):
+            rc = vg.vor_build_async(base + 8 * int(ptr[j]), int(sizes[j]), BOX, plain_opts, wp,
+                                    ws_b, out, stream.cuda_stream)
+            if rc != 0:
+                raise vg.VorError(rc, "plain build")
+            if record:
+                evs[j + 1].record(stream)
+
+    plain(False)
+    torch.cuda.synchronize()
+    plain(True)
+    torch.cuda.synchronize()
+    rc, _ = vg.vor_status(wp, stream.cuda_stream)
+    if rc != 0:
+        raise vg.VorError(rc, "plain builds")
+    lat = np.array([evs[0].elapsed_time(evs[j + 1]) for j in range(S)])
+    plain_ms = float(evs[0].elapsed_time(evs[S]))
+    del wsp, bufs
+    torch.cuda.empty_cache()
+    return {
+        "value": ws_n * S / (ms_max / 1000.0), "unit": "sets/s", "ms_per_step": ms_max,
+        "step_ms": ms, "steps": steps, "warmup": warmup, "n_sets": S, "n_sites": N,
+        "cells_per_s": ws_n * N / (ms_max / 1000.0),
+        "latency_ms": {"batched": {"p50": ms, "p99": ms,
+                                   "note": "every set of a batch completes with the batch"},
+                       "plain": {"p50": float(np.percentile(lat, 50)),
+                                 "p99": float(np.percentile(lat, 99)),
+                                 "note": "sets launched back to back on one stream; latency "
+                                         "from the first launch to the set's completion"}},
+        "plain": {"value": S / (plain_ms / 1000.0), "unit": "sets/s", "ms_total": plain_ms},
+        "speedup_vs_plain": plain_ms / ms,
+        "opts": best.as_dict(), "autotune": {
+            "sample": f"every 7th set ({(S + 6) // 7} sets)", "seconds": tune_s,
+            "candidates": [dict(c.as_dict(), ms=m) for c, m in table]},
+        "graph": "one CUDA graph per batch build (captured once, replayed per step)",
+        "kernels_per_build": per_build, "stages_ms": dict(zip(vg.STAGES, stages)),
+        "stats": stats, "edges": n_edges, "delaunay_edges": n_del, "clocks": clk, "e2e": e2e,
+    }
+
+
+def run_batch(args):
+    import torch
+    ws_n, rank, local = dist_init(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    r = batch_measure(args, dev, args.steps, args.warmup, ws_n)
+    if rank != 0:
+        return 0
+    props = torch.cuda.get_device_properties(dev)
+    sm_mhz = r["clocks"].get("sm_mhz") or 1920.0
+    peak = props.multi_processor_count * 128 * sm_mhz * 1e6 / 1e12
+    st = r["stats"]
+    # the large-cell passes dominate this workload; their candidate evaluations
+    # are the evaluations outside the two thread-per-cell passes
+    ev_large = st["evals"] - st["evals_first_pass"] - st["evals_second_pass"]
+    kms = r["stages_ms"]["large_cells"]
+    achieved = ev_large * OPS_PER_EVAL / (kms / 1000.0) / 1e12
+    line = {
+        "metric": METRIC, "value": r["value"], "unit": "sets/s", "n_gpus": ws_n,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic",
+        "config": {"workload": "batch_4096", "n_sets": r["n_sets"], "n_sites": r["n_sites"],
+                   "sizes": "log-uniform in [16, 65536]",
+                   "distribution": "even sets uniform, odd sets 64-component Gaussian mixture",
+                   "box": BOX, "l2": "256 MiB buffer written between timed steps; inputs 260 MB",
+                   "graph": r["graph"], "opts": r["opts"],
+                   "parallelism": f"replicas x{ws_n}" if ws_n > 1 else "1 GPU"},
+        "latency_ms": r["latency_ms"], "plain": r["plain"],
+        "speedup_vs_plain": r["speedup_vs_plain"], "autotune": r["autotune"],
+        "cells_per_s": r["cells_per_s"], "stages_ms": r["stages_ms"], "stats": st,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "cells_kernel<32,256|1024> (large-cell passes)",
+                     "kernel_ms": kms, "evals_per_launch": ev_large,
+                     "ops_per_eval": OPS_PER_EVAL,
+                     "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x "
+                                   f"{sm_mhz:.0f} MHz median SM clock"},
+        "clocks": r["clocks"], "e2e": r["e2e"],
+        "gpu_launches": r["kernels_per_build"] * args.steps,
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def _serve_stream(vg, reqs, arrivals, cfg_kw, pools):
+    """Submit the requests at their arrival times (seconds from the start;
+    all at once when arrivals is None) to a fresh server and collect every
+    result.  Returns per-request latencies (completion - submission, server
+    clock), the makespan and the server's counters."""
+    import threading
+    import numpy as np
+    srv = vg.Server(**cfg_kw)
+    try:
+        tickets = [None] * len(reqs)
+        t_start = time.perf_counter()
+
+        def submitter():
+            for j, (size, kind, xy) in enumerate(reqs):
+                if arrivals is not None:
+                    d = t_start + arrivals[j] - time.perf_counter()
+                    if d > 0:
+                        time.sleep(d)
+                tickets[j] = srv.submit(xy, BOX, timeout=600.0)
+
+        th = threading.Thread(target=submitter)
+        th.start()
+        lat, t_sub0, t_done_max, waves = [], None, 0.0, []
+        for j in range(len(reqs)):
+            while tickets[j] is None:
+                time.sleep(0.0002)
+            r = srv.wait(tickets[j], timeout=600.0, arrays=False)
+            if r["status"] != 0:
+                raise vg.VorError(r["status"], f"serving request {j}")
+            lat.append(r["t_done"] - r["t_submit"])
+            t_sub0 = r["t_submit"] if t_sub0 is None else min(t_sub0, r["t_submit"])
+            t_done_max = max(t_done_max, r["t_done"])
+            waves.append(r["wave_requests"])
+        th.join()
+        st = srv.stats()
+    finally:
+        srv.close()
+    lat = np.array(lat) * 1000.0
+    return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "makespan_s": t_done_max - t_sub0,
+            "throughput_rps": len(reqs) / (t_done_max - t_sub0),
+            "mean_wave_requests": float(np.mean(waves)), "waves": st["waves"]}
+
+
+def run_serve(args):
+    import numpy as np
+    import torch
+
+    import paper_1212_1095_gb300 as vg
+    import synth
+
+    ws_n = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    pools = synth.serve_pools()
+    n_req = args.requests
+
+    def make(rate, seed):
+        arr, sizes, kinds = synth.poisson_requests(n_req, rate, seed=seed)
+        reqs = [(int(s), int(k), synth.serve_request(j + seed * 100000, s, k, pools))
+                for j, (s, k) in enumerate(zip(sizes, kinds))]
+        return arr, reqs
+
+    ours = dict(device_bytes=48 << 30, host_bytes=8 << 30, max_inflight=4,
+                max_wave_requests=64, max_wave_sites=8 << 20)
+    plain = dict(device_bytes=48 << 30, host_bytes=8 << 30, max_inflight=1,
+                 max_wave_requests=1, max_wave_sites=8 << 20)
+    # warm-up (builds the library's launch shapes, pages the pools in)
+    _, wreqs = make(100.0, synth.SEED_BASE + 50)
+    _serve_stream(vg, wreqs[:max(8, args.warmup * 4)], None, ours, pools)
+    # saturated throughput: every request submitted at once (the burst test)
+    _, sreqs = make(100.0, synth.SEED_BASE + 51)
+    clocks = Clocks(local)
+    clocks.start()
+    sat = _serve_stream(vg, sreqs, None, ours, pools)
+    sat_plain = _serve_stream(vg, sreqs, None, plain, pools)
+    rates = []
+    for frac in (0.5, 0.8):
+        rate = frac * sat["throughput_rps"]
+        arr, reqs = make(rate, synth.SEED_BASE + 52 + int(frac * 10))
+        r_ours = _serve_stream(vg, reqs, arr, ours, pools)
+        r_plain = _serve_stream(vg, reqs, arr, plain, pools)
+        rates.append({"fraction_of_saturation": frac, "rate_rps": rate, "ours": r_ours,
+                      "plain": r_plain})
+    clk = clocks.stop()
+    if rank != 0:
+        return 0
+    mean_size = float(np.mean([s for s, _, _ in sreqs]))
+    line = {
+        "metric": METRIC, "value": sat["throughput_rps"] * ws_n, "unit": "requests/s",
+        "n_gpus": ws_n, "steps": n_req, "warmup": max(8, args.warmup * 4),
+        "ms_per_step": 1000.0 * sat["makespan_s"] / n_req, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": "serve", "requests_per_stream": n_req,
+                   "sizes": "log-uniform in [100, 1000000]", "mean_sites": mean_size,
+                   "distribution": "half uniform, half 64-component Gaussian mixture (slices "
+                                   "of 2^21-site pools)",
+                   "box": BOX, "server": ours, "plain_server": plain,
+                   "parallelism": "1 GPU"},
+        "saturated": {"ours": sat, "plain": sat_plain,
+                      "sites_per_s": sat["throughput_rps"] * mean_size},
+        "poisson": rates,
+        "clocks": clk,
+        "e2e": {"value": sat["throughput_rps"] * ws_n, "unit": "requests/s",
+                "h2d_bytes_per_step": int(8 * mean_size),
+                "d2h_bytes_per_step": None,
+                "note": "every request goes host -> server -> host (results copied into "
+                        "pinned host memory before completion)"},
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -325,6 +679,11 @@ def run_ours(args):
                "d2h_bytes_per_step": 8 * (n + 1) + 20 * ne.value + 8 * nd.value,
                "ms_per_step": 1000.0 * te}
 
+    b = None
+    if args.workload == "uniform_1m" and not args.no_batch:
+        del W
+        torch.cuda.empty_cache()
+        b = batch_measure(args, dev, args.batch_steps, 3, ws_n)
     if rank != 0:
         return 0
     # roofline of the projector kernel: plain ALU work (no tensor cores, the
@@ -363,6 +722,10 @@ def run_ours(args):
     }
     if ws_n == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(xy)
+    if b is not None:
+        line["batched"] = {k: b[k] for k in ("value", "unit", "ms_per_step", "n_sets", "n_sites",
+                                            "latency_ms", "plain", "speedup_vs_plain", "opts",
+                                            "graph", "stages_ms", "e2e")}
     print(json.dumps(line))
     return 0
 
@@ -371,6 +734,10 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch_4096":
+        return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_ours(args)
 
 

@@ -58,6 +58,10 @@ extern "C" {
 #define VOR_E_CUDA (-7)          /* a CUDA runtime call failed               */
 #define VOR_E_INTERNAL (-8)      /* an internal consistency check failed     */
 #define VOR_E_SCRATCH_LIMIT (-9) /* vor_build_noalloc: n needs more than its static scratch */
+#define VOR_E_SERVER_FULL (-10)  /* request larger than a server budget; or submit timed out */
+#define VOR_E_TIMEOUT (-11)      /* vor_server_wait: the request is still pending          */
+#define VOR_E_CANCELLED (-12)    /* the request was cancelled                              */
+#define VOR_PENDING 1            /* vor_server_poll: not finished yet                      */
 
 #define VOR_SIDE_BOTTOM (-1)
 #define VOR_SIDE_RIGHT (-2)
@@ -76,6 +80,8 @@ typedef struct vor_opts {
     int32_t exact_only;       /* 1: skip the float filter, decide every ray exactly      */
     int32_t check_duplicates; /* 1: reject equal sites (VOR_E_DUPLICATE)                  */
     int32_t collect_stats;    /* 1: fill vor_stats (device atomics, slightly slower)      */
+    int32_t bucket_load_pct;  /* automatic bucket side: sites per bucket it aims at around
+                                 a typical site, in hundredths (25..1600); 0: 200          */
 } vor_opts;
 
 /* Counters of one build (filled when collect_stats = 1). */
@@ -92,7 +98,8 @@ typedef struct vor_stats {
     uint64_t widenings;        /* certificate steps that grew the tested region            */
     uint64_t evals_first_pass; /* the part of evals done by the first thread-per-cell pass */
     uint64_t rays_first_pass;  /* the part of rays shot by the first thread-per-cell pass  */
-    uint64_t reserved[4];
+    uint64_t evals_second_pass;/* the part of evals done by the second thread-per-cell pass*/
+    uint64_t reserved[3];
 } vor_stats;
 
 /* Device output buffers, allocated by the caller with the capacities below:
@@ -257,6 +264,98 @@ int vor_build_batch_async(const vor_site *d_sites, const int64_t *d_set_ptr,
                           const vor_box *h_boxes, const vor_opts *opts, void *d_workspace,
                           int64_t ws_bytes, const vor_out *out, int64_t *d_del_set_ptr,
                           void *stream);
+
+/* Autotuner.  Builds the batch once with each of the n_candidates option
+ * sets (one untimed build, then reps timed builds, CUDA events on the
+ * stream) and writes the mean device milliseconds of each to ms[] (a
+ * candidate whose build fails gets +infinity) and the index of the fastest
+ * to *best.  The arguments are those of vor_build_batch_async;
+ * ws_bytes must cover vor_batch_workspace_bytes for every candidate.
+ * vor_autotune_grid writes the default candidates (lanes per cell x disc
+ * size x bucket load) into cand[0..max) and returns how many it wrote.
+ * Synchronous; returns VOR_OK or an argument error. */
+int32_t vor_autotune_grid(vor_opts *cand, int32_t max);
+int vor_autotune_batch(const vor_site *d_sites, const int64_t *d_set_ptr, const int64_t *h_set_ptr,
+                       int32_t n_sets, const vor_box *d_boxes, const vor_box *h_boxes,
+                       const vor_opts *candidates, int32_t n_candidates, int32_t reps,
+                       void *d_workspace, int64_t ws_bytes, const vor_out *out,
+                       int64_t *d_del_set_ptr, void *stream, int32_t *best, float *ms);
+
+/* ---- Serving: a request server with continuous batching ------------------
+ *
+ * The paper has no counterpart; this is the serving driver around the batch
+ * build.  A server owns one device block (its HBM budget), one pinned host
+ * block, a few CUDA streams and one dispatcher thread.  Clients submit point
+ * sets from host memory at any time and collect their diagrams later:
+ *
+ *   - Admission.  A submitted request (its sites copied into the pinned
+ *     block) waits in arrival order.  Whenever a stream is free, the
+ *     dispatcher forms a wave from the longest prefix of waiting requests
+ *     that fits the wave limits and the largest free part of the device
+ *     block (workspace, sites and worst-case outputs of the batch build),
+ *     and launches it: copies in, vor_build_batch_async, status out.
+ *     Requests that arrive while waves run join the next wave (continuous
+ *     batching); waves on different streams overlap on the GPU.
+ *   - Completion.  When a wave's build has finished, its exact result sizes
+ *     are read, a host result block of that size is taken from the pinned
+ *     block, the results are copied into it and the device memory is freed.
+ *   - Errors.  A wave that fails (for instance a site outside its box) is
+ *     split: its requests run again one per wave, so only the faulty request
+ *     reports the error.  A request larger than either budget is refused at
+ *     submission (VOR_E_SERVER_FULL).
+ *
+ * Results stay valid (host pointers into the pinned block) until
+ * vor_server_release.  All functions are thread-safe; CUDA work runs on the
+ * dispatcher thread only, on the device current at vor_server_create. */
+typedef struct vor_server vor_server;
+
+typedef struct vor_server_config {
+    int64_t device_bytes;       /* HBM budget, allocated once at creation          */
+    int64_t host_bytes;         /* pinned host memory for staged sites and results  */
+    int32_t max_inflight;       /* waves on the GPU at once (one stream each), >= 1 */
+    int32_t max_wave_requests;  /* requests per wave, >= 1 (1: no batching)         */
+    int64_t max_wave_sites;     /* sites per wave (a larger single request runs alone) */
+    vor_opts opts;              /* build options of every wave                      */
+    int32_t fail_host_alloc_at; /* fault injection for tests: the k-th result-block
+                                   allocation fails (0: never)                      */
+} vor_server_config;
+
+typedef struct vor_request_result {
+    int32_t status;             /* VOR_OK, VOR_PENDING or a VOR_E_* code             */
+    int32_t wave_requests;      /* requests in the wave that built it                */
+    int64_t n, n_edges, n_del;
+    const int64_t *cell_ptr;    /* host: n + 1 offsets into the edge arrays          */
+    const int32_t *edge_label;  /* host: n_edges labels (indices local to the request) */
+    const double *vx, *vy;      /* host: n_edges vertices                            */
+    const int32_t *del_edge;    /* host: 2 * n_del                                   */
+    double t_submit, t_start, t_done;   /* seconds on the server clock (vor_server_now) */
+} vor_request_result;
+
+typedef struct vor_server_stats {
+    int64_t submitted, completed, failed, cancelled, waves, split_waves, pending, inflight;
+    int64_t max_wave_requests_seen, device_free, device_largest_free, host_free;
+    int64_t reserved[4];
+} vor_server_stats;
+
+void vor_server_config_default(vor_server_config *cfg);
+int vor_server_create(const vor_server_config *cfg, vor_server **out);
+/* Copies the n sites into the server (waits up to timeout_s seconds for room
+ * in the pinned block, else VOR_E_SERVER_FULL) and returns a ticket. */
+int vor_server_submit(vor_server *s, const vor_site *h_sites, int64_t n, vor_box box,
+                      double timeout_s, uint64_t *ticket);
+/* VOR_PENDING while the request runs; else its final status, with res filled. */
+int vor_server_poll(vor_server *s, uint64_t ticket, vor_request_result *res);
+/* Waits up to timeout_s seconds; VOR_E_TIMEOUT if the request is still pending. */
+int vor_server_wait(vor_server *s, uint64_t ticket, double timeout_s, vor_request_result *res);
+/* A waiting request is dropped at once; a running one finishes on the GPU
+ * and its result is discarded.  The ticket's status becomes VOR_E_CANCELLED. */
+int vor_server_cancel(vor_server *s, uint64_t ticket);
+/* Frees the ticket and its result (after a final status). */
+int vor_server_release(vor_server *s, uint64_t ticket);
+int vor_server_statistics(vor_server *s, vor_server_stats *st);
+double vor_server_now(const vor_server *s);
+/* Stops the dispatcher after the running waves, frees everything. */
+int vor_server_destroy(vor_server *s);
 
 /* Number of kernels this library has launched in this process (all builds,
  * all devices; a captured CUDA graph's replays are not counted). */

@@ -25,6 +25,8 @@ __all__ = ["VorOpts", "VorStats", "VorOut", "VorError", "build_library", "librar
            "vor_stage_ms", "STAGES", "build", "build_host", "Diagram", "vor_batch_edge_capacity",
            "vor_batch_delaunay_capacity", "vor_batch_workspace_bytes", "vor_build_batch_async",
            "BatchWorkspace", "BatchDiagram", "build_batch", "vor_kernel_launches",
+           "vor_autotune_grid", "autotune_batch", "Server", "VorServerConfig",
+           "vor_server_config_default",
            "SIDE_BOTTOM", "SIDE_RIGHT", "SIDE_TOP", "SIDE_LEFT"]
 
 SIDE_BOTTOM, SIDE_RIGHT, SIDE_TOP, SIDE_LEFT = -1, -2, -3, -4
@@ -32,7 +34,9 @@ SIDE_BOTTOM, SIDE_RIGHT, SIDE_TOP, SIDE_LEFT = -1, -2, -3, -4
 ERROR_NAMES = {0: "VOR_OK", -1: "VOR_E_INVALID_ARG", -2: "VOR_E_SITE_OUTSIDE",
                -3: "VOR_E_DUPLICATE", -4: "VOR_E_BOX_TOO_LARGE", -5: "VOR_E_OOM",
                -6: "VOR_E_CAPACITY", -7: "VOR_E_CUDA", -8: "VOR_E_INTERNAL",
-               -9: "VOR_E_SCRATCH_LIMIT"}
+               -9: "VOR_E_SCRATCH_LIMIT", -10: "VOR_E_SERVER_FULL", -11: "VOR_E_TIMEOUT",
+               -12: "VOR_E_CANCELLED", 1: "VOR_PENDING"}
+PENDING, E_SERVER_FULL, E_TIMEOUT, E_CANCELLED = 1, -10, -11, -12
 
 
 class VorError(RuntimeError):
@@ -52,7 +56,11 @@ class VorBox(ctypes.Structure):
 class VorOpts(ctypes.Structure):
     _fields_ = [("bucket_side", ctypes.c_int32), ("lanes_per_cell", ctypes.c_int32),
                 ("target", ctypes.c_int32), ("exact_only", ctypes.c_int32),
-                ("check_duplicates", ctypes.c_int32), ("collect_stats", ctypes.c_int32)]
+                ("check_duplicates", ctypes.c_int32), ("collect_stats", ctypes.c_int32),
+                ("bucket_load_pct", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
 
 
 class VorStats(ctypes.Structure):
@@ -62,7 +70,7 @@ class VorStats(ctypes.Structure):
                 ("deferred", ctypes.c_uint64), ("candidates", ctypes.c_uint64),
                 ("max_edges", ctypes.c_uint64), ("widenings", ctypes.c_uint64),
                 ("evals_first_pass", ctypes.c_uint64), ("rays_first_pass", ctypes.c_uint64),
-                ("reserved", ctypes.c_uint64 * 4)]
+                ("evals_second_pass", ctypes.c_uint64), ("reserved", ctypes.c_uint64 * 3)]
 
     def as_dict(self) -> dict:
         return {f: int(getattr(self, f)) for f, _ in self._fields_ if f != "reserved"}
@@ -73,6 +81,32 @@ class VorOut(ctypes.Structure):
                 ("vx", ctypes.c_void_p), ("vy", ctypes.c_void_p),
                 ("del_edge", ctypes.c_void_p), ("totals", ctypes.c_void_p),
                 ("edge_cap", ctypes.c_int64), ("del_cap", ctypes.c_int64)]
+
+
+class VorServerConfig(ctypes.Structure):
+    _fields_ = [("device_bytes", ctypes.c_int64), ("host_bytes", ctypes.c_int64),
+                ("max_inflight", ctypes.c_int32), ("max_wave_requests", ctypes.c_int32),
+                ("max_wave_sites", ctypes.c_int64), ("opts", VorOpts),
+                ("fail_host_alloc_at", ctypes.c_int32)]
+
+
+class VorRequestResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("wave_requests", ctypes.c_int32),
+                ("n", ctypes.c_int64), ("n_edges", ctypes.c_int64), ("n_del", ctypes.c_int64),
+                ("cell_ptr", ctypes.c_void_p), ("edge_label", ctypes.c_void_p),
+                ("vx", ctypes.c_void_p), ("vy", ctypes.c_void_p), ("del_edge", ctypes.c_void_p),
+                ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double),
+                ("t_done", ctypes.c_double)]
+
+
+class VorServerStats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int64) for f in (
+        "submitted", "completed", "failed", "cancelled", "waves", "split_waves", "pending",
+        "inflight", "max_wave_requests_seen", "device_free", "device_largest_free",
+        "host_free")] + [("reserved", ctypes.c_int64 * 4)]
+
+    def as_dict(self) -> dict:
+        return {f: int(getattr(self, f)) for f, _ in self._fields_ if f != "reserved"}
 
 
 _lib = None
@@ -117,6 +151,31 @@ def library():
     lib.vor_batch_workspace_bytes.restype = i64
     lib.vor_build_batch_async.argtypes = [P, P, P, ctypes.c_int32, P, P, P, P, i64, P, P, P]
     lib.vor_build_batch_async.restype = i32
+    lib.vor_autotune_grid.argtypes = [P, ctypes.c_int32]
+    lib.vor_autotune_grid.restype = ctypes.c_int32
+    lib.vor_autotune_batch.argtypes = [P, P, P, ctypes.c_int32, P, P, P, ctypes.c_int32,
+                                       ctypes.c_int32, P, i64, P, P, P, P, P]
+    lib.vor_autotune_batch.restype = i32
+    lib.vor_server_config_default.argtypes = [P]
+    lib.vor_server_config_default.restype = None
+    lib.vor_server_create.argtypes = [P, P]
+    lib.vor_server_create.restype = i32
+    lib.vor_server_submit.argtypes = [P, P, i64, VorBox, ctypes.c_double, P]
+    lib.vor_server_submit.restype = i32
+    lib.vor_server_poll.argtypes = [P, ctypes.c_uint64, P]
+    lib.vor_server_poll.restype = i32
+    lib.vor_server_wait.argtypes = [P, ctypes.c_uint64, ctypes.c_double, P]
+    lib.vor_server_wait.restype = i32
+    lib.vor_server_cancel.argtypes = [P, ctypes.c_uint64]
+    lib.vor_server_cancel.restype = i32
+    lib.vor_server_release.argtypes = [P, ctypes.c_uint64]
+    lib.vor_server_release.restype = i32
+    lib.vor_server_statistics.argtypes = [P, P]
+    lib.vor_server_statistics.restype = i32
+    lib.vor_server_now.argtypes = [P]
+    lib.vor_server_now.restype = ctypes.c_double
+    lib.vor_server_destroy.argtypes = [P]
+    lib.vor_server_destroy.restype = i32
     lib.vor_kernel_launches.argtypes = []
     lib.vor_kernel_launches.restype = i64
     lib.vor_strerror.argtypes = [i32]
@@ -373,10 +432,17 @@ class BatchDiagram:
                        self.delaunay[d0:d1], {})
 
 
+def vor_autotune_grid() -> list:
+    """The library's default autotuner candidates (VorOpts)."""
+    buf = (VorOpts * 64)()
+    k = int(library().vor_autotune_grid(buf, 64))
+    return [buf[i] for i in range(k)]
+
+
 class BatchWorkspace:
     """Device buffers for repeated batch builds with fixed set offsets and boxes."""
 
-    def __init__(self, set_ptr, boxes, opts: VorOpts, device=None):
+    def __init__(self, set_ptr, boxes, opts: VorOpts, device=None, extra_opts=()):
         import numpy as np
         import torch
         self.set_ptr = np.ascontiguousarray(set_ptr, dtype=np.int64)
@@ -387,7 +453,8 @@ class BatchWorkspace:
         self.n = int(self.set_ptr[-1])
         self.opts = opts
         dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
-        nb = vor_batch_workspace_bytes(self.set_ptr, self.boxes, opts)
+        nb = max(vor_batch_workspace_bytes(self.set_ptr, self.boxes, o)
+                 for o in (opts, *extra_opts))
         if nb < 0:
             raise VorError(-1, "vor_batch_workspace_bytes")
         self.ws = torch.empty(nb + 256, dtype=torch.uint8, device=dev)
@@ -445,3 +512,156 @@ def build_batch(sites, set_ptr, boxes, **opts) -> BatchDiagram:
     ws = BatchWorkspace(set_ptr, boxes, vor_opts_default(**opts), device=sites.device)
     ws.launch(sites)
     return ws.finish()
+
+
+def autotune_batch(sites, set_ptr, boxes, candidates=None, reps: int = 2):
+    """Time each candidate option set on this batch (vor_autotune_batch).
+
+    Returns (best VorOpts, list of (VorOpts, mean ms)).  The batch may be a
+    sample of the sets to be built later.
+    """
+    import numpy as np
+    import torch
+    cands = list(candidates) if candidates is not None else vor_autotune_grid()
+    ws = BatchWorkspace(set_ptr, boxes, cands[0], device=sites.device, extra_opts=cands[1:])
+    arr = (VorOpts * len(cands))(*cands)
+    ms = (ctypes.c_float * len(cands))()
+    best = ctypes.c_int32(-1)
+    P = ctypes.c_void_p
+    s = torch.cuda.current_stream()
+    rc = library().vor_autotune_batch(
+        P(sites.data_ptr()), P(ws.d_set_ptr.data_ptr()), P(ws.set_ptr.ctypes.data), ws.n_sets,
+        P(ws.d_boxes.data_ptr()), P(ws.boxes.ctypes.data), arr, len(cands), int(reps),
+        P(ws.ws_ptr), ws.ws_bytes, ctypes.byref(ws.out), P(ws.del_set_ptr.data_ptr()),
+        P(s.cuda_stream), ctypes.byref(best), ms)
+    if rc != 0:
+        raise VorError(rc, "vor_autotune_batch")
+    if best.value < 0:
+        raise VorError(-6, "vor_autotune_batch: no candidate completed")
+    return cands[best.value], [(c, float(ms[i])) for i, c in enumerate(cands)]
+
+
+# ------------------------------------------------------------------ serving ----
+
+def vor_server_config_default(**kw) -> VorServerConfig:
+    """Server configuration with the library defaults; keyword arguments set
+    fields (``opts`` takes a VorOpts)."""
+    c = VorServerConfig()
+    library().vor_server_config_default(ctypes.byref(c))
+    for k, v in kw.items():
+        if v is None:
+            continue
+        if not hasattr(c, k):
+            raise TypeError(f"unknown server option {k}")
+        setattr(c, k, v if k == "opts" else int(v))
+    return c
+
+
+class Server:
+    """The request server of the library (vor_server_*): continuous batching
+    of point sets submitted from host memory.  Results are copied into numpy
+    arrays by ``wait``/``poll`` and the ticket is released unless
+    ``keep=True``."""
+
+    def __init__(self, config: VorServerConfig | None = None, **kw):
+        cfg = config if config is not None else vor_server_config_default(**kw)
+        self._h = ctypes.c_void_p()
+        rc = library().vor_server_create(ctypes.byref(cfg), ctypes.byref(self._h))
+        if rc != 0:
+            raise VorError(rc, "vor_server_create")
+        self.config = cfg
+
+    def submit(self, sites_np, box, timeout: float = 60.0) -> int:
+        import numpy as np
+        a = np.ascontiguousarray(sites_np, dtype=np.int32).reshape(-1, 2)
+        t = ctypes.c_uint64()
+        rc = library().vor_server_submit(self._h, ctypes.c_void_p(a.ctypes.data), a.shape[0],
+                                         _box(box), float(timeout), ctypes.byref(t))
+        if rc != 0:
+            raise VorError(rc, "vor_server_submit")
+        return int(t.value)
+
+    @staticmethod
+    def _result(r: VorRequestResult, arrays: bool = True) -> dict:
+        import numpy as np
+        out = {"status": int(r.status), "n": int(r.n), "wave_requests": int(r.wave_requests),
+               "t_submit": r.t_submit, "t_start": r.t_start, "t_done": r.t_done,
+               "n_edges": int(r.n_edges), "n_del": int(r.n_del)}
+        if r.status == 0 and arrays:
+            def arr(p, ct, count, shape=None):
+                if count == 0:
+                    return np.zeros(shape or (0,), dtype=np.dtype(ct))
+                buf = (ct * count).from_address(p)
+                a = np.frombuffer(buf, dtype=np.dtype(ct)).copy()
+                return a.reshape(shape) if shape else a
+            ne, nd = int(r.n_edges), int(r.n_del)
+            out.update(cell_ptr=arr(r.cell_ptr, ctypes.c_int64, int(r.n) + 1),
+                       labels=arr(r.edge_label, ctypes.c_int32, ne),
+                       vx=arr(r.vx, ctypes.c_double, ne), vy=arr(r.vy, ctypes.c_double, ne),
+                       delaunay=arr(r.del_edge, ctypes.c_int32, 2 * nd, (nd, 2)))
+        return out
+
+    def poll(self, ticket: int, keep: bool = False):
+        """None while pending; else the result dict (status, arrays when ok)."""
+        r = VorRequestResult()
+        r.status = 99                    # untouched by the library for an unknown ticket
+        rc = library().vor_server_poll(self._h, ticket, ctypes.byref(r))
+        if r.status == 99:
+            raise VorError(rc, "vor_server_poll: unknown ticket")
+        if rc == PENDING:
+            return None
+        out = self._result(r)
+        if not keep:
+            self.release(ticket)
+        return out
+
+    def wait(self, ticket: int, timeout: float = 600.0, keep: bool = False,
+             arrays: bool = True) -> dict:
+        """The result dict once final (raises VorError on timeout); with
+        arrays=False only the status, sizes and times."""
+        r = VorRequestResult()
+        r.status = 99
+        rc = library().vor_server_wait(self._h, ticket, float(timeout), ctypes.byref(r))
+        if r.status == 99:
+            raise VorError(rc, "vor_server_wait: unknown ticket")
+        if rc == E_TIMEOUT:
+            raise VorError(rc, "vor_server_wait")
+        out = self._result(r, arrays)
+        if not keep:
+            self.release(ticket)
+        return out
+
+    def cancel(self, ticket: int) -> None:
+        rc = library().vor_server_cancel(self._h, ticket)
+        if rc != 0:
+            raise VorError(rc, "vor_server_cancel")
+
+    def release(self, ticket: int) -> None:
+        rc = library().vor_server_release(self._h, ticket)
+        if rc != 0:
+            raise VorError(rc, "vor_server_release")
+
+    def stats(self) -> dict:
+        st = VorServerStats()
+        library().vor_server_statistics(self._h, ctypes.byref(st))
+        return st.as_dict()
+
+    def now(self) -> float:
+        return float(library().vor_server_now(self._h))
+
+    def close(self) -> None:
+        if self._h:
+            library().vor_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -433,6 +433,8 @@ __global__ void __launch_bounds__(NT) cells_persist_kernel(CellParams P, GatherO
             if (!P.cell_list) {                 // first pass: its own share of the work
                 atomicAdd(&st[STAT_EVALS1], v[2]);
                 atomicAdd(&st[STAT_RAYS1], v[0]);
+            } else {
+                atomicAdd(&st[STAT_EVALS2], v[2]);
             }
         }
     }

@@ -22,7 +22,7 @@ enum : unsigned {
 // per-build counters (vor_stats order)
 enum {
     STAT_RAYS = 0, STAT_VTESTS, STAT_EVALS, STAT_EXACT, STAT_ANNULUS, STAT_RERUNS,
-    STAT_DEFERRED, STAT_CANDIDATES, STAT_MAXE, STAT_WIDEN, STAT_EVALS1, STAT_RAYS1, STAT_N = 16
+    STAT_DEFERRED, STAT_CANDIDATES, STAT_MAXE, STAT_WIDEN, STAT_EVALS1, STAT_RAYS1, STAT_EVALS2, STAT_N = 16
 };
 
 // Workspace header (first 256 bytes of the workspace).
@@ -52,6 +52,8 @@ struct SetMeta {
     int s, m1, m2;          // bucket side and grid (chosen on the device)
     int G;                  // side of the density-probe grid
     int s_min, s_max, s_fixed, m_max;
+    int load_pct;           // sites per bucket the automatic side aims at (hundredths)
+    int pad0;
     double acc;             // probe: sum over the set's sites of log2(coarse count)
 };
 
@@ -144,6 +146,9 @@ __device__ __forceinline__ CellGrid cell_grid(const CellParams &P, int i) {
 // device and kernel; later calls make no CUDA call, so builds can be
 // captured into a CUDA graph after a first (warm-up) build on the device.
 cudaError_t resident_grid(const void *kern, int threads, int smem, int &grid);
+
+// VOR_* status of the error bits of a workspace header (vor_lib.cu)
+int status_of_error_bits(unsigned e);
 
 // Launchers (vor_cells.cu)
 cudaError_t launch_cells_fast(const CellParams &P, int lanes, cudaStream_t st);

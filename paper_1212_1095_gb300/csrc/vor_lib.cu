@@ -17,6 +17,7 @@
 //       scan x2        e_k -> cell_ptr, Delaunay counts -> offsets
 //   K3  compact        CSR edge labels, float64 vertices (Section 5) and the
 //                      Delaunay pairs (Section 6), labels local to the set
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <atomic>
@@ -39,9 +40,9 @@ namespace vor {
 // checked against what the host planned with (hn_total, hm_sum, hg_sum): a
 // mismatch stops the build before any kernel indexes with it.
 __global__ void k_plan(const long long *__restrict__ set_ptr, const vor_box *__restrict__ boxes,
-                       int n_sets, long long n1, vor_box box1, int s_fixed, long long hn_total,
-                       long long hm_sum, long long hg_sum, SetMeta *__restrict__ sets,
-                       WsHeader *hdr);
+                       int n_sets, long long n1, vor_box box1, int s_fixed, int load_pct,
+                       long long hn_total, long long hm_sum, long long hg_sum,
+                       SetMeta *__restrict__ sets, WsHeader *hdr);
 
 // per site: the set it belongs to (binary search in the set offsets)
 __global__ void k_site_set(const long long *__restrict__ set_ptr, int n_sets, int n,
@@ -286,9 +287,9 @@ static void scan(const int *in, int n_max, const int *n_dev, T *out, T *partial,
 // ---------------------------------------------------------------------------
 
 __global__ void k_plan(const long long *__restrict__ set_ptr, const vor_box *__restrict__ boxes,
-                       int n_sets, long long n1, vor_box box1, int s_fixed, long long hn_total,
-                       long long hm_sum, long long hg_sum, SetMeta *__restrict__ sets,
-                       WsHeader *hdr) {
+                       int n_sets, long long n1, vor_box box1, int s_fixed, int load_pct,
+                       long long hn_total, long long hm_sum, long long hg_sum,
+                       SetMeta *__restrict__ sets, WsHeader *hdr) {
     __shared__ long long sh[32];
     long long gcarry = 0, mcarry = 0;
     int bad = 0;
@@ -312,6 +313,7 @@ __global__ void k_plan(const long long *__restrict__ set_ptr, const vor_box *__r
                 M.s_max = pl.s_max;
                 M.s_fixed = s_fixed;
                 M.m_max = pl.m_max;
+                M.load_pct = load_pct;
                 g2 = (long long)pl.G * pl.G;
                 mm = pl.m_max;
             }
@@ -346,7 +348,7 @@ __global__ void k_pick_grid(SetMeta *__restrict__ sets, int n_sets, int s_fixed,
                 if (M.n > 0) {
                     const double cmed = exp2(M.acc / (double)M.n);   // typical sites per coarse cell
                     const double area = ((double)M.W / M.G) * ((double)M.H / M.G);
-                    s = (int)sqrt(2.0 * area / cmed);
+                    s = (int)sqrt(0.01 * M.load_pct * area / cmed);
                 } else {
                     s = M.s_max;
                 }
@@ -477,7 +479,7 @@ __global__ void k_set_del_ptr(const SetMeta *__restrict__ sets, int n_sets, int 
 // ---------------------------------------------------------------------------
 
 struct Layout {
-    int s_fixed, lanes, target, n_sets;
+    int s_fixed, lanes, target, n_sets, load_pct;
     long long n, m_sum, g_sum;
     size_t hdr, sets, sset, bstart, rank, sxy, sid, partial, ecount, dcount, loc, del_ptr, slot,
         spill, deferred, deferred2, deferred3, gcount, grho2, gpos, coarse, total;
@@ -521,6 +523,8 @@ static bool resolve(const int64_t *set_ptr, const vor_box *boxes, int n_sets, in
     if (L.lanes != 1 && L.lanes != 2 && L.lanes != 4 && L.lanes != 8 && L.lanes != 16 && L.lanes != 32) return false;
     L.target = o->target > 0 ? o->target : 22;
     if (L.target > 40) return false;
+    L.load_pct = o->bucket_load_pct > 0 ? o->bucket_load_pct : 200;
+    if (L.load_pct < 25 || L.load_pct > 1600) return false;
     const size_t m = (size_t)L.m_sum;
     const size_t nn = (size_t)(L.n > 0 ? L.n : 1);
     const int nb_b = (int)((m + SCAN_TILE - 1) / SCAN_TILE), nb_n = (int)((nn + SCAN_TILE - 1) / SCAN_TILE);
@@ -609,8 +613,8 @@ static int launch_build(const BatchArgs &A, const vor_opts *o, void *ws, const L
     } count_on_exit{launched};
     mark(0, st);
     if (cudaMemsetAsync(hdr, 0, 256, st) != cudaSuccess) return VOR_E_CUDA;
-    k_plan<<<1, SCAN_T, 0, st>>>(A.set_ptr, A.boxes, L.n_sets, A.n1, A.box1, L.s_fixed, L.n,
-                                 L.m_sum, L.g_sum, sets, hdr);
+    k_plan<<<1, SCAN_T, 0, st>>>(A.set_ptr, A.boxes, L.n_sets, A.n1, A.box1, L.s_fixed, L.load_pct,
+                                 L.n, L.m_sum, L.g_sum, sets, hdr);
     launched++;
     if (n == 0) {
         // nothing but empty sets: empty outputs
@@ -768,6 +772,8 @@ static int map_err(unsigned e) {
     return VOR_OK;
 }
 
+int status_of_error_bits(unsigned e) { return map_err(e); }
+
 }  // namespace vor
 
 using namespace vor;
@@ -782,6 +788,7 @@ void vor_opts_default(vor_opts *o) {
     o->exact_only = 0;
     o->check_duplicates = 1;
     o->collect_stats = 0;
+    o->bucket_load_pct = 0;
 }
 
 int64_t vor_edge_capacity(int64_t n) { return n < 1 ? 0 : 10 * n + 4; }
@@ -866,6 +873,7 @@ int vor_status(const void *d_workspace, void *stream, vor_stats *stats) {
         stats->widenings = h.stats[STAT_WIDEN];
         stats->evals_first_pass = h.stats[STAT_EVALS1];
         stats->rays_first_pass = h.stats[STAT_RAYS1];
+        stats->evals_second_pass = h.stats[STAT_EVALS2];
     }
     return map_err(h.err);
 }
@@ -999,6 +1007,71 @@ int vor_stage_ms(float *ms, int max_stages) {
 
 int64_t vor_kernel_launches(void) { return (int64_t)g_launches.load(); }
 
+int32_t vor_autotune_grid(vor_opts *cand, int32_t max) {
+    // lanes per cell (1: one thread per cell and the two persistent passes;
+    // 8: eight lanes per cell) x first-disc size x bucket load
+    static const int lanes[] = {1, 8};
+    static const int target[] = {16, 22, 28};
+    static const int load[] = {100, 200, 400};
+    int k = 0;
+    for (int a : lanes)
+        for (int b : target)
+            for (int c : load) {
+                if (k < max && cand) {
+                    vor_opts_default(&cand[k]);
+                    cand[k].lanes_per_cell = a;
+                    cand[k].target = b;
+                    cand[k].bucket_load_pct = c;
+                }
+                k++;
+            }
+    return k < max ? k : max;
+}
+
+int vor_autotune_batch(const vor_site *d_sites, const int64_t *d_set_ptr, const int64_t *h_set_ptr,
+                       int32_t n_sets, const vor_box *d_boxes, const vor_box *h_boxes,
+                       const vor_opts *candidates, int32_t n_candidates, int32_t reps,
+                       void *d_workspace, int64_t ws_bytes, const vor_out *out,
+                       int64_t *d_del_set_ptr, void *stream, int32_t *best, float *ms) {
+    if (!candidates || n_candidates < 1 || reps < 1 || !best || !ms) return VOR_E_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return VOR_E_CUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return VOR_E_CUDA;
+    }
+    int rc_all = VOR_OK;
+    *best = -1;
+    for (int c = 0; c < n_candidates; c++) {
+        ms[c] = INFINITY;
+        auto run = [&]() {
+            return vor_build_batch_async(d_sites, d_set_ptr, h_set_ptr, n_sets, d_boxes, h_boxes,
+                                         &candidates[c], d_workspace, ws_bytes, out, d_del_set_ptr,
+                                         stream);
+        };
+        int rc = run();
+        if (rc == VOR_E_INVALID_ARG || rc == VOR_E_BOX_TOO_LARGE) { rc_all = rc; break; }
+        if (rc != VOR_OK || vor_status(d_workspace, stream, nullptr) != VOR_OK) continue;
+        float total = 0.f;
+        bool ok = true;
+        for (int r = 0; r < reps && ok; r++) {
+            float t = 0.f;
+            ok = cudaEventRecord(e0, st) == cudaSuccess && run() == VOR_OK &&
+                 cudaEventRecord(e1, st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+                 cudaEventElapsedTime(&t, e0, e1) == cudaSuccess &&
+                 vor_status(d_workspace, stream, nullptr) == VOR_OK;
+            total += t;
+        }
+        if (!ok) continue;
+        ms[c] = total / reps;
+        if (*best < 0 || ms[c] < ms[*best]) *best = c;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc_all;
+}
+
 const char *vor_strerror(int code) {
     switch (code) {
     case VOR_OK: return "ok";
@@ -1011,6 +1084,10 @@ const char *vor_strerror(int code) {
     case VOR_E_CUDA: return "CUDA runtime error";
     case VOR_E_INTERNAL: return "internal consistency check failed";
     case VOR_E_SCRATCH_LIMIT: return "n needs more workspace than the static scratch of vor_build_noalloc";
+    case VOR_E_SERVER_FULL: return "request larger than a server budget, or no room before the timeout";
+    case VOR_E_TIMEOUT: return "the request is still pending";
+    case VOR_E_CANCELLED: return "the request was cancelled";
+    case VOR_PENDING: return "pending";
     default: return "unknown error";
     }
 }

@@ -344,3 +344,31 @@ def batch_workload(cache: bool = True):
         np.savez(tmp, xy=xy, ptr=ptr)
         os.replace(tmp, path)
     return xy, ptr
+
+
+def serve_pools(cache: bool = True):
+    """Site pools of the serving workload: 2^21 uniform and 2^21 Gaussian
+    mixture sites in [0, 2^20]^2, in random order, so that a contiguous
+    slice of a pool is a random sample of its distribution."""
+    import os
+    seed = SEED_BASE + 6
+    path = os.path.join(_cache_dir(), f"serve_pools_{seed}.npz") if cache else None
+    if path and os.path.exists(path):
+        d = np.load(path)
+        return d["uniform"], d["clustered"]
+    u = uniform_sites(1 << 21, seed=seed)
+    g = gaussian_mixture_sites(1 << 21, seed=seed + 1)
+    if path:
+        tmp = path + f".{os.getpid()}.npz"
+        np.savez(tmp, uniform=u, clustered=g)
+        os.replace(tmp, path)
+    return u, g
+
+
+def serve_request(j: int, size: int, kind: int, pools, seed: int = SEED_BASE + 7) -> np.ndarray:
+    """Request j of the serving workload: `size` sites, a contiguous slice of
+    the uniform (kind 0) or clustered (kind 1) pool at a seeded offset."""
+    pool = pools[int(kind)]
+    span = pool.shape[0] - int(size)
+    off = int(splitmix64(seed, 40, 1, j)[0] % np.uint64(span + 1))
+    return pool[off:off + int(size)]

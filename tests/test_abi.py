@@ -66,3 +66,26 @@ def test_no_cpu_fallback_in_the_package():
                 src = open(os.path.join(root, f)).read()
                 assert "import oracle" not in src and "from oracle" not in src, f
                 assert "vor_oracle" not in src, f
+
+
+def test_batch_sizing_and_autotune_grid_on_the_host(lib):
+    import numpy as np
+    o = vg.vor_opts_default()
+    assert o.bucket_load_pct == 0
+    ptr = np.array([0, 10, 10, 4000], dtype=np.int64)
+    boxes = np.array([[1000, 1000], [50, 50], [1 << 20, 1 << 20]], dtype=np.int32)
+    nb = vg.vor_batch_workspace_bytes(ptr, boxes, o)
+    assert nb > vg.vor_workspace_bytes(3990, 1 << 20, o)
+    # offsets that decrease, a box too large, a bucket load out of range
+    assert vg.vor_batch_workspace_bytes(np.array([0, 10, 5]), boxes[:2], o) == -1
+    assert vg.vor_batch_workspace_bytes(ptr, np.array([[1000, 1000], [50, 50], [1 << 21, 8]]), o) == -1
+    assert vg.vor_batch_workspace_bytes(ptr, boxes, vg.vor_opts_default(bucket_load_pct=10)) == -1
+    assert vg.vor_batch_edge_capacity(4000, 3) == 10 * 4000 + 12
+    assert vg.vor_batch_delaunay_capacity(4000, 3) == 3 * 4000 + 3
+    grid = vg.vor_autotune_grid()
+    assert len(grid) == 18
+    assert {g.lanes_per_cell for g in grid} == {1, 8}
+    assert {g.bucket_load_pct for g in grid} == {100, 200, 400}
+    for g in grid:
+        assert vg.vor_batch_workspace_bytes(ptr, boxes, g) > 0
+    assert vg.vor_kernel_launches() >= 0

@@ -154,3 +154,39 @@ def test_batch_graph_capture_and_replay():
         for j in range(12):
             s = inp[ptr[j]:ptr[j + 1]]
             assert_full_parity(to_numpy(B.set(j)), _oracle(s, synth.WORLD))
+
+
+def test_bucket_load_option_keeps_results():
+    sets, boxes = _mixed_sets()
+    keep = [3, 6, 7, 9]
+    sets = [sets[j] for j in keep]
+    boxes = [boxes[j] for j in keep]
+    xy, ptr, bx = _pack(sets, boxes)
+    ref = None
+    for load in (25, 100, 400, 1600):
+        B = vg.build_batch(torch.from_numpy(xy).cuda(), ptr, bx, bucket_load_pct=load)
+        got = [to_numpy(B.set(j)) for j in range(len(sets))]
+        if ref is None:
+            ref = got
+            for j, (s, box) in enumerate(zip(sets, boxes)):
+                assert_full_parity(got[j], _oracle(s, box))
+        else:
+            for a, b in zip(ref, got):
+                for key in a:
+                    assert np.array_equal(a[key], b[key])
+
+
+def test_autotune_returns_the_fastest_valid_candidate():
+    xy, ptr = synth.batch_sets(n_sets=32, lo=16, hi=4096, seed=synth.SEED_BASE + 41)
+    bx = np.full((32, 2), synth.WORLD, dtype=np.int32)
+    cands = [vg.vor_opts_default(), vg.vor_opts_default(lanes_per_cell=8, target=16),
+             vg.vor_opts_default(bucket_load_pct=400)]
+    best, table = vg.autotune_batch(torch.from_numpy(xy).cuda(), ptr, bx, candidates=cands, reps=1)
+    ms = [m for _, m in table]
+    assert all(np.isfinite(ms))
+    assert best.as_dict() == cands[int(np.argmin(ms))].as_dict()
+    B = vg.build_batch(torch.from_numpy(xy).cuda(), ptr, bx, **{
+        k: v for k, v in best.as_dict().items() if k in ("lanes_per_cell", "target",
+                                                          "bucket_load_pct")})
+    for j in range(32):
+        assert_full_parity(to_numpy(B.set(j)), _oracle(xy[ptr[j]:ptr[j + 1]], synth.WORLD))
