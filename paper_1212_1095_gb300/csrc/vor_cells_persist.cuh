@@ -21,22 +21,35 @@
 
 namespace vor {
 
-constexpr int P_NT = 64, P_SMAX = 16, P_EMAX = 32, P_RMAX = 32;
+constexpr int P_NT = 64, P_SMAX = 16, P_EMAX = 16, P_RMAX = 32;
 constexpr int P_REFILL = 8;          // idle lanes that trigger a batched refill
 // first pass: 4 sides + up to 40 sites; second pass (the cells the first
 // disc did not certify): a disc with about 2.2 times the sites, 4 + 72 entries
 constexpr int P1_CMAX = 44, P2_CMAX = 76;
 
+// cp.async (sm_80+): an 8-byte copy from global to shared memory that runs
+// without registers; wait_all waits for this thread's copies only
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
 struct GatherOut {
     int *count;        // sites in the disc per cell (-1: more than gmax, or t >= cap)
     long long *rho2;   // squared disc radius per cell
-    int *pos;          // gmax sorted positions per cell
+    float2 *tab;       // gmax candidates per cell: (nx, ny) = site - p, as floats (exact)
+    int *lab;          // gmax labels per cell: the site's index in its set
     int gmax;
-    int cap;           // cells the position buffer holds (later cells go to the next pass)
+    int cap;           // cells the lists hold (later cells go to the next pass)
 };
 
 // One thread per cell: the cells are the sorted positions t < P.n, or
-// P.cell_list[t] for t < *P.list_count; outputs are indexed by t.
+// P.cell_list[t] for t < *P.list_count; outputs are indexed by t.  Each
+// candidate is written in the form the projector's table holds, so loading a
+// cell is a plain copy.
 __global__ void __launch_bounds__(256) gather_kernel(CellParams P, GatherOut G, float target) {
     if (P.hdr->err) return;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -63,7 +76,8 @@ __global__ void __launch_bounds__(256) gather_kernel(CellParams P, GatherOut G, 
     const int bx0 = p.x - r <= 0 ? 0 : (p.x - r) / s, bx1 = min(g.m1 - 1, (p.x + r) / s);
     const int by0 = p.y - r <= 0 ? 0 : (p.y - r) / s, by1 = min(g.m2 - 1, (p.y + r) / s);
     int cnt = 0;
-    int *dst = G.pos + (size_t)t * G.gmax;
+    float2 *dtab = G.tab + (size_t)t * G.gmax;
+    int *dlab = G.lab + (size_t)t * G.gmax;
     for (int row = by0; row <= by1; row++) {
         const int a = g.bs[row * g.m1 + bx0], b = g.bs[row * g.m1 + bx1 + 1];
         for (int pos = a; pos < b; pos++) {
@@ -71,7 +85,10 @@ __global__ void __launch_bounds__(256) gather_kernel(CellParams P, GatherOut G, 
             const int2 q = P.sxy[pos];
             const int nx = q.x - p.x, ny = q.y - p.y;
             if ((i64)nx * nx + (i64)ny * ny > rho2) continue;
-            if (cnt < G.gmax) dst[cnt] = pos;
+            if (cnt < G.gmax) {
+                dtab[cnt] = t1::cand_of(nx, ny);
+                dlab[cnt] = P.sid[pos] - g.site_base;
+            }
             cnt++;
         }
     }
@@ -81,27 +98,57 @@ __global__ void __launch_bounds__(256) gather_kernel(CellParams P, GatherOut G, 
 
 template <int NT, int CMAX, int SMAX, int EMAX, int RMAX>
 __global__ void __launch_bounds__(NT) cells_persist_kernel(CellParams P, GatherOut G) {
-    extern __shared__ __align__(16) float4 tbl_raw[];
+    extern __shared__ __align__(16) float2 tbl_raw[];
     if (P.hdr->err) return;
     const t1::Table<NT> T{tbl_raw + threadIdx.x};
     const unsigned FULL = 0xffffffffu;
-    int cpos[CMAX];
-    long long stx[SMAX], sty[SMAX];
-    unsigned char scw[SMAX], sccw[SMAX];
-    unsigned char emit[EMAX];
+    static_assert(EMAX <= 16, "edge labels are packed into two 64-bit registers");
+    // Per-thread state lives in registers.  The edge list (candidate indices,
+    // one byte each) is packed into em0/em1.  The subedge stack keeps its top
+    // four entries in registers (s0 = the top) and only deeper entries in the
+    // local arrays, which few cells reach.
+    unsigned long long em0 = 0, em1 = 0;
+    auto emit_get = [&](int q) -> int {
+        return (int)(((q < 8 ? em0 : em1) >> ((q & 7) * 8)) & 0xff);
+    };
+    auto emit_put = [&](int q, int lab) {
+        const unsigned long long v = (unsigned long long)lab << ((q & 7) * 8);
+        if (q < 8) em0 |= v; else em1 |= v;
+    };
+    i64 s0x = 0, s0y = 0, s1x = 0, s1y = 0, s2x = 0, s2y = 0, s3x = 0, s3y = 0;
+    int s0l = 0, s1l = 0, s2l = 0, s3l = 0;           // clockwise line | counter-clockwise << 8
+    long long dsx[SMAX], dsy[SMAX];
+    int dsl[SMAX];
+    int sp = 0;
+    auto push = [&](i64 x, i64 y, int cw, int ccw) {
+        if (sp >= 4) { dsx[sp - 4] = s3x; dsy[sp - 4] = s3y; dsl[sp - 4] = s3l; }
+        s3x = s2x; s3y = s2y; s3l = s2l;
+        s2x = s1x; s2y = s1y; s2l = s1l;
+        s1x = s0x; s1y = s0y; s1l = s0l;
+        s0x = x; s0y = y; s0l = cw | (ccw << 8);
+        sp++;
+    };
+    auto pop = [&]() {
+        s0x = s1x; s0y = s1y; s0l = s1l;
+        s1x = s2x; s1y = s2y; s1l = s2l;
+        s2x = s3x; s2y = s3y; s2l = s3l;
+        if (sp > 4) { s3x = dsx[sp - 5]; s3y = dsy[sp - 5]; s3l = dsl[sp - 5]; }
+        sp--;
+    };
     t1::Counters cnt{};
     const int stride = gridDim.x * NT;
     int t = blockIdx.x * NT + threadIdx.x;
     const int total = P.cell_list ? *P.list_count : P.n;
 
     // state of the thread's current cell
-    int i = -1, C = 0;
+    int i = -1, C = 0, ctt = 0;      // ctt: the cell's entry in the gather lists
+    int kcell = 0;                   // the cell's index in the batch
     int2 p = make_int2(0, 0);
     int cW = 0, cH = 0, cbase = 0;   // the cell's box and the first site of its set
     i64 rho2 = 0;
     int phase = 0, h0c = -1, h0w = -1, h1c = -1, h1w = -1;
     i64 lx = 0, ly = 0;
-    int llab = -1, sp = 0, ne = 0, rays = 3, first = -1, last = -1;
+    int llab = -1, ne = 0, rays = 3, first = -1, last = -1;
     bool have = false;     // a cell is loaded and its projector runs
     bool fin = false;      // the projector finished: certificate and output pending
     bool ok = true;        // the projector stayed within the capacities
@@ -128,8 +175,8 @@ __global__ void __launch_bounds__(NT) cells_persist_kernel(CellParams P, GatherO
                         for (int q = 0; q < e; q++) {
                             int n1x, n1y, n2x, n2y;
                             i64 c1, c2, Nx, Ny, D;
-                            T.line(emit[q], n1x, n1y, c1);
-                            T.line(emit[q + 1 < e ? q + 1 : 0], n2x, n2y, c2);
+                            T.line(emit_get(q), n1x, n1y, c1);
+                            T.line(emit_get(q + 1 < e ? q + 1 : 0), n2x, n2y, c2);
                             intersect(n1x, n1y, c1, n2x, n2y, c2, Nx, Ny, D);
                             if (D == 0) { defer = true; break; }
                             const float rd = 1.f / (float)D;
@@ -144,12 +191,12 @@ __global__ void __launch_bounds__(NT) cells_persist_kernel(CellParams P, GatherO
                         // canonical order: start at the smallest normal angle
                         int start = 0, bxn, byn, qx, qy;
                         i64 dummy;
-                        T.line(emit[0], bxn, byn, dummy);
+                        T.line(emit_get(0), bxn, byn, dummy);
                         for (int q = 1; q < e; q++) {
-                            T.line(emit[q], qx, qy, dummy);
+                            T.line(emit_get(q), qx, qy, dummy);
                             if (angle_less(qx, qy, bxn, byn)) { start = q; bxn = qx; byn = qy; }
                         }
-                        const int k = P.sid[i];
+                        const int k = kcell;
                         const int kl = k - cbase;
                         int *dst;
                         int off = -1;
@@ -161,14 +208,26 @@ __global__ void __launch_bounds__(NT) cells_persist_kernel(CellParams P, GatherO
                             dst = P.spill + off;
                         }
                         if (!defer) {
+                            // labels from the gather list, eight independent loads
+                            // at a time
+                            const int *__restrict__ gl = G.lab + (size_t)ctt * G.gmax - 4;
                             int dcnt = 0;
-                            for (int q = 0; q < e; q++) {
-                                int qq = start + q;
-                                if (qq >= e) qq -= e;
-                                const int c = emit[qq];
-                                const int l = c < 4 ? -1 - c : P.sid[cpos[c]] - cbase;
-                                dst[q] = l;
-                                dcnt += l > kl ? 1 : 0;
+                            for (int q0 = 0; q0 < e; q0 += 8) {
+                                int lq[8];
+#pragma unroll
+                                for (int u = 0; u < 8; u++) {
+                                    int qq = start + q0 + u;
+                                    if (qq >= e) qq -= e;
+                                    const int c = q0 + u < e ? emit_get(qq) : 0;
+                                    lq[u] = c >= 4 ? __ldg(gl + c) : -1 - c;
+                                }
+#pragma unroll
+                                for (int u = 0; u < 8; u++) {
+                                    if (q0 + u < e) {
+                                        dst[q0 + u] = lq[u];
+                                        dcnt += lq[u] > kl ? 1 : 0;
+                                    }
+                                }
                             }
                             P.ecount[k] = e;
                             P.dcount[k] = dcnt;
@@ -203,6 +262,7 @@ __global__ void __launch_bounds__(NT) cells_persist_kernel(CellParams P, GatherO
                         continue;
                     }
                     p = P.sxy[i];
+                    kcell = __ldg(P.sid + i);
                     rho2 = G.rho2[tt];
                     {
                         const SetMeta &M = set_of(P.sets, P.sset, i);
@@ -210,20 +270,20 @@ __global__ void __launch_bounds__(NT) cells_persist_kernel(CellParams P, GatherO
                         cH = M.H;
                         cbase = (int)M.site_base;
                     }
-                    T.put(0, t1::cand_of(0, -p.y, true));
-                    T.put(1, t1::cand_of(cW - p.x, 0, true));
-                    T.put(2, t1::cand_of(0, cH - p.y, true));
-                    T.put(3, t1::cand_of(-p.x, 0, true));
-                    const int *src = G.pos + (size_t)tt * G.gmax;
-                    for (int q = 0; q < nc; q++) {
-                        const int pos = src[q];
-                        const int2 a = P.sxy[pos];
-                        T.put(4 + q, t1::cand_of(a.x - p.x, a.y - p.y, false));
-                        cpos[4 + q] = pos;
-                    }
+                    T.put(0, t1::cand_of(0, -p.y));
+                    T.put(1, t1::cand_of(cW - p.x, 0));
+                    T.put(2, t1::cand_of(0, cH - p.y));
+                    T.put(3, t1::cand_of(-p.x, 0));
+                    // the candidates: asynchronous 8-byte copies straight into
+                    // the table, all in flight at once
+                    const float2 *src = G.tab + (size_t)tt * G.gmax;
+                    for (int q = 0; q < nc; q++) cp_async8(&tbl_raw[(4 + q) * NT + threadIdx.x], src + q);
+                    cp_async_wait_all();
+                    ctt = tt;
                     C = nc + 4;
                     cnt.cands += C;
                     phase = 0; sp = 0; ne = 0; rays = 3; first = -1; last = -1; llab = -1;
+                    em0 = em1 = 0;
                     ok = true;
                     have = true;
                     break;
@@ -244,18 +304,17 @@ __global__ void __launch_bounds__(NT) cells_persist_kernel(CellParams P, GatherO
                 query = true;
             } else {
                 while (sp > 0) {
-                    const int top = sp - 1;
-                    const i64 rx = stx[top], ry = sty[top];
-                    const int rcw = scw[top];
+                    const i64 rx = s0x, ry = s0y;
+                    const int rcw = s0l & 0xff;
                     if (llab == rcw) {                           // same line: no vertex
                         if (llab != last) {
                             if (ne >= EMAX) { ok = false; sp = 0; break; }
-                            emit[ne++] = (unsigned char)llab;
+                            emit_put(ne++, llab);
                             if (first < 0) first = llab;
                             last = llab;
                         }
-                        lx = rx; ly = ry; llab = sccw[top];
-                        sp--;
+                        lx = rx; ly = ry; llab = s0l >> 8;
+                        pop();
                         continue;
                     }
                     int n1x, n1y, n2x, n2y;
@@ -301,23 +360,28 @@ __global__ void __launch_bounds__(NT) cells_persist_kernel(CellParams P, GatherO
         float u1a = -FLT_MAX, u2a = -FLT_MAX, lsa = -FLT_MAX, uxa = -FLT_MAX;
         float u1b = -FLT_MAX, u2b = -FLT_MAX, lsb = -FLT_MAX, uxb = -FLT_MAX;
         int i1a = -1, i1b = -1;
-        int c = 0;
+        if (Cq > 0) {                                    // the four sides
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+                float Ua, La;
+                t1::filter_keys(T.get(c), true, fx, fy, eth, Ua, La);
+                if (Ua > u1a) { u2a = u1a; u1a = Ua; i1a = c; lsa = La; } else u2a = fmaxf(u2a, Ua);
+                if (c != la && c != lb) uxa = fmaxf(uxa, Ua);
+            }
+        }
+        int c = 4;
         for (; c + 1 < Cq; c += 2) {
-            const float4 qa = T.get(c), qb = T.get(c + 1);
-            const float da = fmaf(qa.x, fx, qa.y * fy), db = fmaf(qb.x, fx, qb.y * fy);
-            const float ta = qa.w * eth, tb = qb.w * eth;
-            const float Ua = fmaf(da, qa.z, ta), La = fmaf(da, qa.z, -ta);
-            const float Ub = fmaf(db, qb.z, tb), Lb = fmaf(db, qb.z, -tb);
+            float Ua, La, Ub, Lb;
+            t1::filter_keys(T.get(c), false, fx, fy, eth, Ua, La);
+            t1::filter_keys(T.get(c + 1), false, fx, fy, eth, Ub, Lb);
             if (Ua > u1a) { u2a = u1a; u1a = Ua; i1a = c; lsa = La; } else u2a = fmaxf(u2a, Ua);
             if (Ub > u1b) { u2b = u1b; u1b = Ub; i1b = c + 1; lsb = Lb; } else u2b = fmaxf(u2b, Ub);
             if (c != la && c != lb) uxa = fmaxf(uxa, Ua);
             if (c + 1 != la && c + 1 != lb) uxb = fmaxf(uxb, Ub);
         }
         if (c < Cq) {
-            const float4 qa = T.get(c);
-            const float da = fmaf(qa.x, fx, qa.y * fy);
-            const float ta = qa.w * eth;
-            const float Ua = fmaf(da, qa.z, ta), La = fmaf(da, qa.z, -ta);
+            float Ua, La;
+            t1::filter_keys(T.get(c), false, fx, fy, eth, Ua, La);
             if (Ua > u1a) { u2a = u1a; u1a = Ua; i1a = c; lsa = La; } else u2a = fmaxf(u2a, Ua);
             if (c != la && c != lb) uxa = fmaxf(uxa, Ua);
         }
@@ -349,9 +413,9 @@ __global__ void __launch_bounds__(NT) cells_persist_kernel(CellParams P, GatherO
                 for (int q = 0; q < C && !viol; q++) {
                     if (q == la || q == lb) continue;
                     if (!P.exact_only) {
-                        const float4 g = T.get(q);
-                        const float den = fmaf(g.x, fx, g.y * fy);
-                        if (fmaf(den, g.z, g.w * eth) < klo) continue;
+                        float Ug, Lg;
+                        t1::filter_keys(T.get(q), q < 4, fx, fy, eth, Ug, Lg);
+                        if (Ug < klo) continue;
                     }
                     int nx, ny;
                     i64 cc;
@@ -379,32 +443,30 @@ __global__ void __launch_bounds__(NT) cells_persist_kernel(CellParams P, GatherO
             else if (phase == 1) { h1c = hc; h1w = hw; }
             else {
                 lx = 2; ly = -1; llab = h0c;
-                stx[0] = 2;  sty[0] = -1; scw[0] = (unsigned char)h0w; sccw[0] = (unsigned char)h0c;
-                stx[1] = -2; sty[1] = -1; scw[1] = (unsigned char)hw;  sccw[1] = (unsigned char)hc;
-                stx[2] = 0;  sty[2] = 1;  scw[2] = (unsigned char)h1w; sccw[2] = (unsigned char)h1c;
-                sp = 3;
+                sp = 0;
+                push(2, -1, h0w, h0c);
+                push(-2, -1, hw, hc);
+                push(0, 1, h1w, h1c);
             }
             phase++;
         } else if (inside) {                               // u is a vertex: L1, L2 are edges
-            const int top = sp - 1;
             if (la != last) {
                 if (ne >= EMAX) { ok = false; have = false; fin = true; continue; }
-                emit[ne++] = (unsigned char)la;
+                emit_put(ne++, la);
                 if (first < 0) first = la;
                 last = la;
             }
             if (lb != last) {
                 if (ne >= EMAX) { ok = false; have = false; fin = true; continue; }
-                emit[ne++] = (unsigned char)lb;
+                emit_put(ne++, lb);
                 if (first < 0) first = lb;
                 last = lb;
             }
-            lx = stx[top]; ly = sty[top]; llab = sccw[top];
-            sp--;
+            lx = s0x; ly = s0y; llab = s0l >> 8;
+            pop();
         } else {                                           // divide the subedge at theta_3
             if (sp >= SMAX || ++rays > RMAX || hc < 0) { ok = false; have = false; fin = true; continue; }
-            stx[sp] = tx; sty[sp] = ty; scw[sp] = (unsigned char)hw; sccw[sp] = (unsigned char)hc;
-            sp++;
+            push(tx, ty, hw, hc);
         }
     }
     if (P.collect_stats) {

@@ -3,20 +3,21 @@
 
 namespace vor {
 
-static GatherOut gather_out(const CellParams &P, int pass, int *gcount, long long *grho2, int *gpos) {
-    // both passes share one position buffer of n * (P1_CMAX - 4) entries; the
-    // second pass lists fewer cells (the deferred ones) with more sites each
+static GatherOut gather_out(const CellParams &P, int pass, int *gcount, long long *grho2,
+                            float2 *gtab, int *glab) {
+    // both passes share lists of n * (P1_CMAX - 4) entries; the second pass
+    // lists fewer cells (the deferred ones) with more sites each
     const long long entries = (long long)P.n * (P1_CMAX - 4);
-    if (pass == 1) return GatherOut{gcount, grho2, gpos, P1_CMAX - 4, P.n};
-    return GatherOut{gcount, grho2, gpos, P2_CMAX - 4, (int)(entries / (P2_CMAX - 4))};
+    if (pass == 1) return GatherOut{gcount, grho2, gtab, glab, P1_CMAX - 4, P.n};
+    return GatherOut{gcount, grho2, gtab, glab, P2_CMAX - 4, (int)(entries / (P2_CMAX - 4))};
 }
 
-cudaError_t launch_gather_pass(const CellParams &P, int pass, int *gcount, long long *grho2, int *gpos,
-                               cudaStream_t st) {
+cudaError_t launch_gather_pass(const CellParams &P, int pass, int *gcount, long long *grho2,
+                               float2 *gtab, int *glab, cudaStream_t st) {
     const int total_max = P.cell_list ? P.n_list : P.n;
     const float target = pass == 1 ? (float)P.target : 2.2f * (float)P.target;
-    gather_kernel<<<(total_max + 255) / 256, 256, 0, st>>>(P, gather_out(P, pass, gcount, grho2, gpos),
-                                                          target);
+    gather_kernel<<<(total_max + 255) / 256, 256, 0, st>>>(
+        P, gather_out(P, pass, gcount, grho2, gtab, glab), target);
     return cudaGetLastError();
 }
 
@@ -24,7 +25,7 @@ template <int CMAX>
 static cudaError_t launch_persist(const CellParams &P, const GatherOut &G, cudaStream_t st) {
     const int total_max = P.cell_list ? P.n_list : P.n;
     auto kern = cells_persist_kernel<P_NT, CMAX, P_SMAX, P_EMAX, P_RMAX>;
-    const int smem = P_NT * CMAX * (int)sizeof(float4);
+    const int smem = P_NT * CMAX * (int)sizeof(float2);
     int resident = 0;
     cudaError_t e = resident_grid((const void *)kern, P_NT, smem, resident);
     if (e != cudaSuccess) return e;
@@ -36,9 +37,9 @@ static cudaError_t launch_persist(const CellParams &P, const GatherOut &G, cudaS
     return cudaGetLastError();
 }
 
-cudaError_t launch_cells_pass(const CellParams &P, int pass, int *gcount, long long *grho2, int *gpos,
-                              cudaStream_t st) {
-    const GatherOut G = gather_out(P, pass, gcount, grho2, gpos);
+cudaError_t launch_cells_pass(const CellParams &P, int pass, int *gcount, long long *grho2,
+                              float2 *gtab, int *glab, cudaStream_t st) {
+    const GatherOut G = gather_out(P, pass, gcount, grho2, gtab, glab);
     return pass == 1 ? launch_persist<P1_CMAX>(P, G, st) : launch_persist<P2_CMAX>(P, G, st);
 }
 

@@ -21,24 +21,46 @@ struct Counters {
 
 enum { OK = 0, DEFER = 1, FAIL = 2 };
 
-// candidate c of this thread: cb[c * NT] = (nx, ny, 1/c, (|nx|+|ny|)/c)
+// candidate c of this thread: cb[c * NT] = (nx, ny), the line 2 <n, v - p> = c
+// with c = |n|^2 (a site) or 2 |n|^2 (a side of X, candidates 0..3)
 template <int NT>
 struct Table {
-    float4 *cb;
-    __device__ __forceinline__ float4 get(int c) const { return cb[c * NT]; }
-    __device__ __forceinline__ void put(int c, float4 v) const { cb[c * NT] = v; }
+    float2 *cb;
+    __device__ __forceinline__ float2 get(int c) const { return cb[c * NT]; }
+    __device__ __forceinline__ void put(int c, float2 v) const { cb[c * NT] = v; }
     __device__ __forceinline__ void line(int c, int &nx, int &ny, i64 &cc) const {
-        const float4 q = get(c);
+        const float2 q = get(c);
         nx = __float2int_rn(q.x);
         ny = __float2int_rn(q.y);
         cc = line_c(nx, ny, c < 4);
     }
 };
 
-__device__ __forceinline__ float4 cand_of(int nx, int ny, bool side) {
-    const float cf = (float)line_c(nx, ny, side);
-    const float rc = 1.f / cf;
-    return make_float4((float)nx, (float)ny, rc, (float)(abs(nx) + abs(ny)) * rc);
+__device__ __forceinline__ float2 cand_of(int nx, int ny) { return make_float2((float)nx, (float)ny); }
+
+// reciprocal, PTX rcp.approx (maximum error 1 ulp over the whole range); the
+// argument here is at least 1, so flushing denormals changes nothing
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Float filter of a candidate for the direction (fx, fy) = theta rounded to
+// float: bounds U >= K >= L of its key K = <n, theta> / c.  The computed key
+// errs by at most about 8u (|nx||tx| + |ny||ty|) / c (u = 2^-24: theta
+// rounded to float, the dot product, c = nx^2 + ny^2 rounded, the 1-ulp
+// reciprocal, the product); the tolerance (|nx| + |ny|) / c * max(|tx|,|ty|)
+// * 2^-19 is 32u times an upper bound of the same factor, a margin of 4x
+// that also covers the rounding of the tolerance and of k +- tol.
+__device__ __forceinline__ void filter_keys(float2 q, bool side, float fx, float fy, float eth,
+                                            float &U, float &L) {
+    const float cf = fmaf(q.x, q.x, q.y * q.y) * (side ? 2.f : 1.f);
+    const float rc = rcp_approx(cf);
+    const float den = fmaf(q.x, fx, q.y * fy);
+    const float tol = (fabsf(q.x) + fabsf(q.y)) * rc * eth;
+    U = fmaf(den, rc, tol);
+    L = fmaf(den, rc, -tol);
 }
 
 // a strictly more counter-clockwise than b (normals in one open half-plane)
@@ -61,10 +83,10 @@ __device__ void exact_argmax(const Table<NT> &T, int C, i64 tx, i64 ty, float fx
     i128 bd = 0;
     i64 bc = 1;
     for (int c = 0; c < C; c++) {
-        const float4 q = T.get(c);
         if (use_thr) {
-            const float den = fmaf(q.x, fx, q.y * fy);
-            if (!(fmaf(den, q.z, q.w * eth) >= thr)) continue;
+            float U, L;
+            filter_keys(T.get(c), c < 4, fx, fy, eth, U, L);
+            if (!(U >= thr)) continue;
         }
         int nx, ny;
         i64 cc;

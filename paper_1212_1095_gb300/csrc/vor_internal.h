@@ -154,10 +154,10 @@ int status_of_error_bits(unsigned e);
 cudaError_t launch_cells_fast(const CellParams &P, int lanes, cudaStream_t st);
 // one thread per cell; pass 1 over all cells, pass 2 over the list
 // P.cell_list: first the candidate gather, then the persistent projector
-cudaError_t launch_gather_pass(const CellParams &P, int pass, int *gcount, long long *grho2, int *gpos,
-                               cudaStream_t st);
-cudaError_t launch_cells_pass(const CellParams &P, int pass, int *gcount, long long *grho2, int *gpos,
-                              cudaStream_t st);
+cudaError_t launch_gather_pass(const CellParams &P, int pass, int *gcount, long long *grho2,
+                               float2 *gtab, int *glab, cudaStream_t st);
+cudaError_t launch_cells_pass(const CellParams &P, int pass, int *gcount, long long *grho2,
+                              float2 *gtab, int *glab, cudaStream_t st);
 int pass_gather_width();
 // one warp per cell over P.cell_list, cells taken from *P.next_cell; tier 0:
 // medium capacities (defers to P.deferred), tier 1: large capacities

@@ -482,7 +482,7 @@ struct Layout {
     int s_fixed, lanes, target, n_sets, load_pct;
     long long n, m_sum, g_sum;
     size_t hdr, sets, sset, bstart, rank, sxy, sid, partial, ecount, dcount, loc, del_ptr, slot,
-        spill, deferred, deferred2, deferred3, gcount, grho2, gpos, coarse, total;
+        spill, deferred, deferred2, deferred3, gcount, grho2, gtab, glab, coarse, total;
     int spill_cap;
     int n_partial;
 };
@@ -550,7 +550,8 @@ static bool resolve(const int64_t *set_ptr, const vor_box *boxes, int n_sets, in
     L.deferred3 = at; at = align256(at + nn * 4);
     L.gcount = at;   at = align256(at + nn * 4);
     L.grho2 = at;    at = align256(at + nn * 8);
-    L.gpos = at;     at = align256(at + nn * 4 * (size_t)pass_gather_width());
+    L.gtab = at;     at = align256(at + nn * 8 * (size_t)pass_gather_width());
+    L.glab = at;     at = align256(at + nn * 4 * (size_t)pass_gather_width());
     L.coarse = at;   at = align256(at + (size_t)L.g_sum * 4);
     L.total = at;
     return true;
@@ -663,15 +664,16 @@ static int launch_build(const BatchArgs &A, const vor_opts *o, void *ws, const L
     P.cell_list = nullptr; P.list_count = nullptr; P.n_list = 0;
     P.hdr = hdr;
     if (L.lanes == 1) {
-        int *gcount = (int *)(base + L.gcount), *gpos = (int *)(base + L.gpos);
+        int *gcount = (int *)(base + L.gcount), *glab = (int *)(base + L.glab);
+        float2 *gtab = (float2 *)(base + L.gtab);
         long long *grho2 = (long long *)(base + L.grho2);
         // first pass over all cells: the cells its disc does not certify
         // (or that exceed its table) go on to the second pass
         P.deferred = deferred;
         P.deferred_count = &hdr->ndeferred;
-        if (launch_gather_pass(P, 1, gcount, grho2, gpos, st) != cudaSuccess) return VOR_E_CUDA;
+        if (launch_gather_pass(P, 1, gcount, grho2, gtab, glab, st) != cudaSuccess) return VOR_E_CUDA;
         mark(2, st);
-        if (launch_cells_pass(P, 1, gcount, grho2, gpos, st) != cudaSuccess) return VOR_E_CUDA;
+        if (launch_cells_pass(P, 1, gcount, grho2, gtab, glab, st) != cudaSuccess) return VOR_E_CUDA;
         mark(3, st);
         // second pass: a disc with about 2.2 times the sites
         CellParams P2 = P;
@@ -680,8 +682,8 @@ static int launch_build(const BatchArgs &A, const vor_opts *o, void *ws, const L
         P2.n_list = n;
         P2.deferred = deferred2;
         P2.deferred_count = &hdr->ndeferred2;
-        if (launch_gather_pass(P2, 2, gcount, grho2, gpos, st) != cudaSuccess) return VOR_E_CUDA;
-        if (launch_cells_pass(P2, 2, gcount, grho2, gpos, st) != cudaSuccess) return VOR_E_CUDA;
+        if (launch_gather_pass(P2, 2, gcount, grho2, gtab, glab, st) != cudaSuccess) return VOR_E_CUDA;
+        if (launch_cells_pass(P2, 2, gcount, grho2, gtab, glab, st) != cudaSuccess) return VOR_E_CUDA;
         launched += 4;                // two gathers, two persistent passes
         mark(4, st);
     } else {
