@@ -49,51 +49,76 @@ struct GatherOut {
 // One thread per cell: the cells are the sorted positions t < P.n, or
 // P.cell_list[t] for t < *P.list_count; outputs are indexed by t.  Each
 // candidate is written in the form the projector's table holds, so loading a
-// cell is a plain copy.
-__global__ void __launch_bounds__(256) gather_kernel(CellParams P, GatherOut G, float target) {
+// cell is a plain copy.  A block stages its cells' lists in shared memory
+// (one padded row per cell) and writes them out as one contiguous range.
+template <int NT, int GMAX>
+__global__ void __launch_bounds__(NT) gather_kernel(CellParams P, GatherOut G, float target) {
+    __shared__ float2 stab[NT * (GMAX + 1)];
+    __shared__ int slab[NT * (GMAX + 1)];
     if (P.hdr->err) return;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int total = P.cell_list ? *P.list_count : P.n;
-    if (t >= total) return;
-    if (t >= G.cap) { G.count[t] = -1; return; }
-    const int i = P.cell_list ? P.cell_list[t] : t;
-    const int2 p = P.sxy[i];
-    const CellGrid g = cell_grid(P, i);
-    const int s = g.s;
-    const int bx = p.x / s, by = p.y / s;
-    int c9 = 0, nb9 = 0;
-    {
-        const int x0 = max(bx - 1, 0), x1 = min(bx + 1, g.m1 - 1);
-        for (int row = max(by - 1, 0); row <= min(by + 1, g.m2 - 1); row++) {
-            c9 += g.bs[row * g.m1 + x1 + 1] - g.bs[row * g.m1 + x0];
-            nb9 += x1 - x0 + 1;
-        }
-    }
-    const float area = (float)nb9 * (float)s * (float)s;
-    i64 rho2 = (i64)(target * area / (3.14159265f * (float)max(c9 - 1, 1)));
-    rho2 = max(min(rho2, (i64)(16.f * (float)s * (float)s)), (i64)4);
-    const int r = (int)ceilf(sqrtf((float)rho2)) + 1;
-    const int bx0 = p.x - r <= 0 ? 0 : (p.x - r) / s, bx1 = min(g.m1 - 1, (p.x + r) / s);
-    const int by0 = p.y - r <= 0 ? 0 : (p.y - r) / s, by1 = min(g.m2 - 1, (p.y + r) / s);
-    int cnt = 0;
-    float2 *dtab = G.tab + (size_t)t * G.gmax;
-    int *dlab = G.lab + (size_t)t * G.gmax;
-    for (int row = by0; row <= by1; row++) {
-        const int a = g.bs[row * g.m1 + bx0], b = g.bs[row * g.m1 + bx1 + 1];
-        for (int pos = a; pos < b; pos++) {
-            if (pos == i) continue;
-            const int2 q = P.sxy[pos];
-            const int nx = q.x - p.x, ny = q.y - p.y;
-            if ((i64)nx * nx + (i64)ny * ny > rho2) continue;
-            if (cnt < G.gmax) {
-                dtab[cnt] = t1::cand_of(nx, ny);
-                dlab[cnt] = P.sid[pos] - g.site_base;
+    const int t0 = blockIdx.x * NT;
+    if (t0 >= total) return;
+    const int t = t0 + threadIdx.x;
+    float2 *rtab = stab + threadIdx.x * (GMAX + 1);
+    int *rlab = slab + threadIdx.x * (GMAX + 1);
+    if (t < total && t >= G.cap) G.count[t] = -1;
+    if (t < total && t < G.cap) {
+        const int i = P.cell_list ? P.cell_list[t] : t;
+        const int2 p = P.sxy[i];
+        const CellGrid g = cell_grid(P, i);
+        const int s = g.s;
+        const int bx = p.x / s, by = p.y / s;
+        int c9 = 0, nb9 = 0;
+        {
+            const int x0 = max(bx - 1, 0), x1 = min(bx + 1, g.m1 - 1);
+            for (int row = max(by - 1, 0); row <= min(by + 1, g.m2 - 1); row++) {
+                c9 += g.bs[row * g.m1 + x1 + 1] - g.bs[row * g.m1 + x0];
+                nb9 += x1 - x0 + 1;
             }
-            cnt++;
         }
+        const float area = (float)nb9 * (float)s * (float)s;
+        i64 rho2 = (i64)(target * area / (3.14159265f * (float)max(c9 - 1, 1)));
+        rho2 = max(min(rho2, (i64)(16.f * (float)s * (float)s)), (i64)4);
+        const int r = (int)ceilf(sqrtf((float)rho2)) + 1;
+        const int by0 = p.y - r <= 0 ? 0 : (p.y - r) / s, by1 = min(g.m2 - 1, (p.y + r) / s);
+        int cnt = 0;
+        for (int row = by0; row <= by1; row++) {
+            // the buckets of this row that meet the disc (its chord, widened)
+            const i64 ylo = (i64)row * s, yhi = ylo + s;
+            const i64 dy = p.y < ylo ? ylo - p.y : (p.y > yhi ? p.y - yhi : 0);
+            if (dy * dy > rho2) continue;
+            const float h = sqrtf((float)(rho2 - dy * dy)) + 1.f;
+            const int bx0 = max(0, (int)floorf(((float)p.x - h) / (float)s));
+            const int bx1 = min(g.m1 - 1, (int)floorf(((float)p.x + h) / (float)s));
+            if (bx0 > bx1) continue;
+            const int a = g.bs[row * g.m1 + bx0], b = g.bs[row * g.m1 + bx1 + 1];
+            for (int pos = a; pos < b; pos++) {
+                if (pos == i) continue;
+                const int2 q = P.sxy[pos];
+                const int nx = q.x - p.x, ny = q.y - p.y;
+                if ((i64)nx * nx + (i64)ny * ny > rho2) continue;
+                if (cnt < GMAX) {
+                    rtab[cnt] = t1::cand_of(nx, ny);
+                    rlab[cnt] = __ldg(P.sid + pos) - g.site_base;
+                }
+                cnt++;
+            }
+        }
+        G.count[t] = cnt > GMAX ? -1 : cnt;
+        G.rho2[t] = rho2;
     }
-    G.count[t] = cnt > G.gmax ? -1 : cnt;
-    G.rho2[t] = rho2;
+    __syncthreads();
+    // the block's rows [t0, t0 + rows) are contiguous in the lists
+    const int rows = min(min(total, G.cap), t0 + NT) - t0;
+    if (rows <= 0) return;
+    float2 *gt = G.tab + (size_t)t0 * GMAX;
+    int *gl = G.lab + (size_t)t0 * GMAX;
+    for (int idx = threadIdx.x; idx < rows * GMAX; idx += NT) {
+        const int rr = idx / GMAX, q = idx - rr * GMAX;
+        gt[idx] = stab[rr * (GMAX + 1) + q];
+        gl[idx] = slab[rr * (GMAX + 1) + q];
+    }
 }
 
 template <int NT, int CMAX, int SMAX, int EMAX, int RMAX>

@@ -15,9 +15,11 @@ static GatherOut gather_out(const CellParams &P, int pass, int *gcount, long lon
 cudaError_t launch_gather_pass(const CellParams &P, int pass, int *gcount, long long *grho2,
                                float2 *gtab, int *glab, cudaStream_t st) {
     const int total_max = P.cell_list ? P.n_list : P.n;
-    const float target = pass == 1 ? (float)P.target : 2.2f * (float)P.target;
-    gather_kernel<<<(total_max + 255) / 256, 256, 0, st>>>(
-        P, gather_out(P, pass, gcount, grho2, gtab, glab), target);
+    const GatherOut G = gather_out(P, pass, gcount, grho2, gtab, glab);
+    if (pass == 1)
+        gather_kernel<64, P1_CMAX - 4><<<(total_max + 63) / 64, 64, 0, st>>>(P, G, (float)P.target);
+    else
+        gather_kernel<32, P2_CMAX - 4><<<(total_max + 31) / 32, 32, 0, st>>>(P, G, 2.2f * (float)P.target);
     return cudaGetLastError();
 }
 

@@ -410,6 +410,28 @@ __device__ __forceinline__ void line_of(const int2 *set_sites, int W, int H, int
     }
 }
 
+// 1/d for a nonzero integer-valued double |d| < 2^44: a float seed from PTX
+// rcp.approx (relative error below 2^-22 after rounding d to float) refined
+// by two Newton steps in double (error squared each step: below 2^-44, then
+// the rounding of double).
+__device__ __forceinline__ double recip_d(double d) {
+    float r0;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"((float)d));
+    double r = (double)r0;
+    r = fma(r, fma(-d, r, 1.0), r);
+    r = fma(r, fma(-d, r, 1.0), r);
+    return r;
+}
+
+// a / d from r ~ 1/d: the product, then one correction with its exact
+// residual a - q d (one FMA), which leaves the quotient within half an ulp
+// or so; an exactly representable quotient (an integer vertex) comes out
+// exact.  Well inside the 1e-9 relative tolerance of the vertices.
+__device__ __forceinline__ double div_by(double a, double d, double r) {
+    const double q = a * r;
+    return fma(fma(-q, d, a), r, q);
+}
+
 __global__ void k_compact(CompactParams Q) {
     if (Q.hdr->err) return;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -448,8 +470,9 @@ __global__ void k_compact(CompactParams Q) {
         const i64 numx = (i64)((unsigned long long)p.x * (unsigned long long)D + (unsigned long long)Nx);
         const i64 numy = (i64)((unsigned long long)p.y * (unsigned long long)D + (unsigned long long)Ny);
         Q.edge_label[off + q] = a_lab;
-        Q.vx[off + q] = (double)numx / (double)D;
-        Q.vy[off + q] = (double)numy / (double)D;
+        const double dD = (double)D, rD = recip_d(dD);
+        Q.vx[off + q] = div_by((double)numx, dD, rD);
+        Q.vy[off + q] = div_by((double)numy, dD, rD);
         // Delaunay pair (k, a) for a > k at rank = number of smaller such labels
         if (a_lab > kl) {
             int rank = 0;
