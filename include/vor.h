@@ -99,7 +99,9 @@ typedef struct vor_stats {
     uint64_t evals_first_pass; /* the part of evals done by the first thread-per-cell pass */
     uint64_t rays_first_pass;  /* the part of rays shot by the first thread-per-cell pass  */
     uint64_t evals_second_pass;/* the part of evals done by the second thread-per-cell pass*/
-    uint64_t reserved[3];
+    uint64_t medium_cells;     /* cells handed to the warp-per-cell medium tier            */
+    uint64_t large_cells;      /* cells handed on to the warp-per-cell large tier          */
+    uint64_t reserved[1];
 } vor_stats;
 
 /* Device output buffers, allocated by the caller with the capacities below:

@@ -56,6 +56,7 @@ struct __align__(16) GroupSmem {
     short tmp[EMAX];             // scratch of the candidate compaction
     int ncand;                   // candidate count while appending
     int flag;
+    int hist[32];                // certificate: cutters per distance bin of the annulus
 };
 
 struct Hit { int ccw, cw; };
@@ -346,47 +347,63 @@ __device__ int projector(GroupSmem<CMAX, SMAX, EMAX> &S, const int C, const int 
 }
 
 // Walk the sites of the bucket rows by0..by1 with the G lanes of a group.
-// row_span(row, x0, x1) names the buckets of a row to visit (false: none).
-// Each lane reads the site range of one row; a prefix sum of the range
-// lengths over the group then lets the lanes take consecutive sites of the
-// concatenated ranges, so rows of unequal length keep every lane busy and
-// the rows' offset loads overlap instead of following one another.
-// visit(pos) runs once per site position.  Returns the sites visited.
-template <int G, class RowSpan, class Visit>
-__device__ __forceinline__ int scan_rows(const CellGrid &g, int by0, int by1, int gl, unsigned gmask,
-                                         RowSpan row_span, Visit visit) {
+// row_spans(row, x0, x1) writes up to NSPAN disjoint bucket ranges of a row
+// to visit (in ascending order) and returns how many.  Each lane reads the
+// site ranges of one row; for every span slot a prefix sum of the range
+// lengths over the group lets the lanes take consecutive sites of the
+// concatenated ranges, ILP per lane per step with their loads in flight, so
+// rows of unequal length keep every lane busy and the loads overlap.
+// visit(pos, site) runs once per site position.  Returns the sites visited.
+template <int G, int NSPAN, int ILP, class RowSpans, class Visit>
+__device__ __forceinline__ int scan_rows(const CellGrid &g, const int2 *__restrict__ sxy, int by0,
+                                         int by1, int gl, unsigned gmask, RowSpans row_spans,
+                                         Visit visit) {
     int seen = 0;
     for (int r0 = by0; r0 <= by1; r0 += G) {
         const int row = r0 + gl;
-        int a = 0, len = 0;
-        if (row <= by1) {
-            int x0 = 0, x1 = -1;
-            if (row_span(row, x0, x1) && x0 <= x1) {
-                const int *rb = g.bs + (size_t)row * g.m1;
-                a = rb[x0];
-                len = rb[x1 + 1] - a;
-            }
-        }
-        int incl = len;
+        int x0[NSPAN], x1[NSPAN];
+        int ns = 0;
+        if (row <= by1) ns = row_spans(row, x0, x1);
+        int nmax = ns;
 #pragma unroll
-        for (int off = 1; off < G; off <<= 1) {
-            const int y = __shfl_up_sync(gmask, incl, off, G);
-            if (gl >= off) incl += y;
-        }
-        const int total = __shfl_sync(gmask, incl, G - 1, G);
-        const int excl = incl - len;
-        seen += total;
-        for (int k0 = 0; k0 < total; k0 += G) {
-            const int k = k0 + gl;
-            int j = 0;                       // the last lane whose range starts at or before k
+        for (int off = G / 2; off > 0; off >>= 1) nmax = max(nmax, __shfl_xor_sync(gmask, nmax, off, G));
+        const int *rb = g.bs + (size_t)(row <= by1 ? row : by0) * g.m1;
 #pragma unroll
-            for (int step = G / 2; step > 0; step >>= 1) {
-                const int ex = __shfl_sync(gmask, excl, j + step, G);
-                if (ex <= k) j += step;
+        for (int k = 0; k < NSPAN; k++) {
+            if (k >= nmax) break;
+            int a = 0, len = 0;
+            if (k < ns) {
+                a = rb[x0[k]];
+                len = rb[x1[k] + 1] - a;
             }
-            const int aj = __shfl_sync(gmask, a, j, G);
-            const int ej = __shfl_sync(gmask, excl, j, G);
-            if (k < total) visit(aj + (k - ej));
+            int incl = len;
+#pragma unroll
+            for (int off = 1; off < G; off <<= 1) {
+                const int y = __shfl_up_sync(gmask, incl, off, G);
+                if (gl >= off) incl += y;
+            }
+            const int total = __shfl_sync(gmask, incl, G - 1, G);
+            const int excl = incl - len;
+            seen += total;
+            for (int k0 = 0; k0 < total; k0 += ILP * G) {
+                int pk[ILP];
+                int2 sk[ILP];
+#pragma unroll
+                for (int u = 0; u < ILP; u++) {
+                    const int kk = k0 + u * G + gl;
+                    int j = 0;               // the last lane whose range starts at or before kk
+#pragma unroll
+                    for (int step = G / 2; step > 0; step >>= 1) {
+                        const int ex = __shfl_sync(gmask, excl, j + step, G);
+                        if (ex <= kk) j += step;
+                    }
+                    pk[u] = __shfl_sync(gmask, a, j, G) + kk - __shfl_sync(gmask, excl, j, G);
+                    sk[u] = kk < total ? sxy[pk[u]] : make_int2(0, 0);
+                }
+#pragma unroll
+                for (int u = 0; u < ILP; u++)
+                    if (k0 + u * G + gl < total) visit(pk[u], sk[u]);
+            }
         }
     }
     return seen;
@@ -403,6 +420,118 @@ __device__ __forceinline__ bool disc_row_span(const CellGrid &g, int row, int cx
     x0 = max(0, (int)floorf(((float)cx - h) / (float)g.s));
     x1 = min(g.m1 - 1, (int)floorf(((float)cx + h) / (float)g.s));
     return true;
+}
+
+// The parts of a row that can hold a site cutting the polygon (vertices
+// S.vx/S.vy relative to p, padded radii S.vr) within the annulus
+// r2lo < |a - p|^2 <= r2hi, as up to 4 disjoint ascending bucket ranges:
+// the union of the vertex discs' chords (merged into at most 4 intervals; a
+// fifth is folded into its nearest neighbour, which only widens the range),
+// clipped to the outer disc's chord, less the part of the inner disc's
+// chord that lies inside the inner disc over the whole band.  Every range
+// is a superset of what it must cover; sites are tested exactly afterwards.
+template <class SM>
+__device__ int flower_row_spans(const CellGrid &g, const SM &S, int e, int2 p, i64 r2lo, i64 r2hi,
+                                int row, int *x0, int *x1) {
+    constexpr int K = 4;
+    const float s = (float)g.s;
+    const i64 ylo = (i64)row * g.s, yhi = ylo + g.s;
+    const i64 dy = p.y < ylo ? ylo - p.y : (p.y > yhi ? p.y - yhi : 0);
+    if (dy * dy > r2hi) return 0;
+    const float ho = sqrtf((float)(r2hi - dy * dy)) + 1.f;
+    const float olo = (float)p.x - ho, ohi = (float)p.x + ho;
+    float lo[K], hi[K];
+    int nk = 0;
+    const float fylo = (float)ylo, fyhi = (float)yhi;
+    for (int v = 0; v < e; v++) {
+        const float vxa = (float)p.x + S.vx[v], vya = (float)p.y + S.vy[v], rv = S.vr[v];
+        const float dv = fmaxf(0.f, fmaxf(fylo - vya, vya - fyhi));
+        if (dv > rv) continue;
+        const float h = sqrtf(fmaxf(rv * rv - dv * dv, 0.f)) + 1.f;
+        float a = fmaxf(vxa - h, olo), b = fminf(vxa + h, ohi);
+        if (a > b) continue;
+        // merge into an overlapping interval, else append, else fold into
+        // the nearest one
+        int hit = -1;
+        float best = FLT_MAX;
+        int near = 0;
+#pragma unroll
+        for (int j = 0; j < K; j++) {
+            if (j < nk) {
+                if (hit < 0 && a <= hi[j] && lo[j] <= b) hit = j;
+                const float gap = fmaxf(lo[j] - b, a - hi[j]);
+                if (gap < best) { best = gap; near = j; }
+            }
+        }
+        if (hit < 0 && nk < K) {
+#pragma unroll
+            for (int j = 0; j < K; j++) if (j == nk) { lo[j] = a; hi[j] = b; }
+            nk++;
+            continue;
+        }
+        const int j0 = hit >= 0 ? hit : near;
+#pragma unroll
+        for (int j = 0; j < K; j++)
+            if (j == j0) { lo[j] = fminf(lo[j], a); hi[j] = fmaxf(hi[j], b); }
+    }
+    if (nk == 0) return 0;
+    // sort (insertion, K small), then merge overlapping intervals
+#pragma unroll
+    for (int x = 1; x < K; x++) {
+#pragma unroll
+        for (int y = x; y > 0; y--) {
+            if (y < nk && lo[y] < lo[y - 1]) {
+                const float tl = lo[y], th = hi[y];
+                lo[y] = lo[y - 1]; hi[y] = hi[y - 1];
+                lo[y - 1] = tl; hi[y - 1] = th;
+            }
+        }
+    }
+    // the inner disc over the whole band: |dy| is at most dyf there
+    const i64 dyf = max(llabs(ylo - p.y), llabs(yhi - p.y));
+    float ilo = 1.f, ihi = 0.f;                          // empty
+    if (dyf * dyf < r2lo) {
+        const float hin = sqrtf((float)(r2lo - dyf * dyf)) - 2.f;
+        if (hin > 0.f) { ilo = (float)p.x - hin; ihi = (float)p.x + hin; }
+    }
+    // bucket ranges, merged where they touch, with the inner part removed
+    int n = 0;
+    int cx0 = 0, cx1 = -1;                               // the range being built
+    auto emit_range = [&](float a, float b) {
+        if (a > b) return;
+        const int bx0 = max(0, (int)floorf(a / s)), bx1 = min(g.m1 - 1, (int)floorf(b / s));
+        if (bx0 > bx1) return;
+        if (cx1 >= cx0 && bx0 <= cx1 + 1) { cx0 = min(cx0, bx0); cx1 = max(cx1, bx1); return; }
+        if (cx1 >= cx0) {
+#pragma unroll
+            for (int j = 0; j < K + 1; j++) if (j == n) { x0[j] = cx0; x1[j] = cx1; }
+            n++;
+        }
+        cx0 = bx0;
+        cx1 = bx1;
+    };
+#pragma unroll
+    for (int j = 0; j < K; j++) {
+        if (j >= nk) break;
+        const float a = lo[j], b = hi[j];
+        if (ilo <= ihi && a < ilo && b > ihi) {          // the inner part splits it
+            emit_range(a, ilo);
+            emit_range(ihi, b);
+        } else if (ilo <= ihi && a >= ilo && b <= ihi) {  // entirely inside the inner disc
+        } else if (ilo <= ihi && a < ilo && b >= ilo) {
+            emit_range(a, ilo);
+        } else if (ilo <= ihi && a <= ihi && b > ihi) {
+            emit_range(ihi, b);
+        } else {
+            emit_range(a, b);
+        }
+    }
+    if (cx1 >= cx0) {
+#pragma unroll
+        for (int j = 0; j < K + 1; j++) if (j == n) { x0[j] = cx0; x1[j] = cx1; }
+        n++;
+    }
+    return n;
 }
 
 // Does the site n = a - p (c = |n|^2) cut the polygon of e vertices in
@@ -437,7 +566,9 @@ __device__ __forceinline__ bool cuts_polygon(const SM &S, int e, int nx, int ny,
 // vertices.  With flower, only the parts of the rows that meet some vertex
 // disc (S.vr radii) are read: a site outside every vertex disc cannot cut.
 // Uses S.ncand as the append counter and sets S.flag when the table would
-// grow past cap.  Returns the number of sites examined.
+// grow past cap; with cut_only the cutters are also counted per distance
+// bin in S.hist (32 bins of |a - p|^2 over (r2lo, r2hi]).  Returns the
+// number of sites examined.
 template <int G, int CMAX, int SMAX, int EMAX>
 __device__ int scan_disc(const CellParams &P, const CellGrid &g, GroupSmem<CMAX, SMAX, EMAX> &S,
                          const int2 p, const int self, const i64 r2lo, const i64 r2hi,
@@ -447,34 +578,17 @@ __device__ int scan_disc(const CellParams &P, const CellGrid &g, GroupSmem<CMAX,
     const int r = (int)ceilf(sqrtf((float)r2hi)) + 1;
     const int by0 = p.y - r <= 0 ? 0 : (p.y - r) / s;
     const int by1 = min(g.m2 - 1, (p.y + r) / s);
-    auto span = [&](int row, int &x0, int &x1) -> bool {
-        if (!disc_row_span(g, row, p.x, p.y, r2hi, x0, x1)) return false;
-        if (!flower) return true;
-        // bounding x-range of the vertex-disc chords in this row
-        const float ylo = (float)row * (float)s, yhi = ylo + (float)s;
-        float ulo = FLT_MAX, uhi = -FLT_MAX;
-        for (int v = 0; v < e; v++) {
-            const float vxa = (float)p.x + S.vx[v], vya = (float)p.y + S.vy[v], rv = S.vr[v];
-            const float dv = fmaxf(0.f, fmaxf(ylo - vya, vya - yhi));
-            if (dv > rv) continue;
-            const float h = sqrtf(fmaxf(rv * rv - dv * dv, 0.f)) + 1.f;
-            ulo = fminf(ulo, vxa - h);
-            uhi = fmaxf(uhi, vxa + h);
-        }
-        if (ulo > uhi) return false;
-        x0 = max(x0, (int)floorf(fmaxf(ulo, -1.f) / (float)s));
-        x1 = min(x1, (int)floorf(fminf(uhi, (float)g.W + 1.f) / (float)s));
-        return true;
-    };
-    auto visit = [&](int pos) {
+    const float binscale = 32.f / (float)max(r2hi - r2lo, (i64)1);
+    auto visit = [&](int pos, int2 q) {
         if (pos == self) return;
-        const int2 q = P.sxy[pos];
         const int nx = q.x - p.x, ny = q.y - p.y;
         const i64 cc = (i64)nx * nx + (i64)ny * ny;
         if (cc <= r2lo || cc > r2hi) return;
         if (cut_only) {
             cnt.annulus++;
             if (!cuts_polygon(S, e, nx, ny, cc)) return;
+            const int bin = min(31, max(0, (int)((float)(cc - r2lo) * binscale)));
+            atomicAdd(&S.hist[bin], 1);
         }
         const int at = atomicAdd(&S.ncand, 1);
         if (at < cap) {
@@ -485,7 +599,37 @@ __device__ int scan_disc(const CellParams &P, const CellGrid &g, GroupSmem<CMAX,
             S.flag = 1;
         }
     };
-    return scan_rows<G>(g, by0, by1, gl, gmask, span, visit);
+    if (flower && CMAX >= 1024) {
+        auto spans = [&](int row, int *x0, int *x1) -> int {
+            return flower_row_spans(g, S, e, p, r2lo, r2hi, row, x0, x1);
+        };
+        return scan_rows<G, 5, 2>(g, P.sxy, by0, by1, gl, gmask, spans, visit);
+    }
+    if (flower) {
+        // the bounding x-range of the vertex-disc chords in this row
+        auto span = [&](int row, int *x0, int *x1) -> int {
+            if (!disc_row_span(g, row, p.x, p.y, r2hi, x0[0], x1[0])) return 0;
+            const float ylo = (float)row * (float)s, yhi = ylo + (float)s;
+            float ulo = FLT_MAX, uhi = -FLT_MAX;
+            for (int v = 0; v < e; v++) {
+                const float vxa = (float)p.x + S.vx[v], vya = (float)p.y + S.vy[v], rv = S.vr[v];
+                const float dv = fmaxf(0.f, fmaxf(ylo - vya, vya - yhi));
+                if (dv > rv) continue;
+                const float h = sqrtf(fmaxf(rv * rv - dv * dv, 0.f)) + 1.f;
+                ulo = fminf(ulo, vxa - h);
+                uhi = fmaxf(uhi, vxa + h);
+            }
+            if (ulo > uhi) return 0;
+            x0[0] = max(x0[0], (int)floorf(fmaxf(ulo, -1.f) / (float)s));
+            x1[0] = min(x1[0], (int)floorf(fminf(uhi, (float)g.W + 1.f) / (float)s));
+            return x0[0] <= x1[0] ? 1 : 0;
+        };
+        return scan_rows<G, 1, 1>(g, P.sxy, by0, by1, gl, gmask, span, visit);
+    }
+    auto span = [&](int row, int *x0, int *x1) -> int {
+        return disc_row_span(g, row, p.x, p.y, r2hi, x0[0], x1[0]) && x0[0] <= x1[0] ? 1 : 0;
+    };
+    return scan_rows<G, 1, 1>(g, P.sxy, by0, by1, gl, gmask, span, visit);
 }
 
 // vertices of the polygon (S.emit, e edges) into S.vx/S.vy; returns max |v-p|^2
@@ -570,14 +714,27 @@ __device__ int certify_by_vertex_discs(const CellParams &P, const CellGrid &g,
         C = e;
         cnt.widen++;
         i64 step2 = min(min(need, rho2 < ((i64)1 << 60) / 4 ? 4 * rho2 + 4 : rho2), far2);
+        // the medium tier reads one bounding range per bucket row; a wide
+        // annulus goes to the large tier, which reads the vertex-disc chords
+        // row by row
+        if (CMAX < 1024 && 2.f * sqrtf((float)step2) > 256.f * (float)g.s) return CELL_DEFER;
         for (int shrink = 0;; shrink++) {
             if (gl == 0) { S.ncand = C; S.flag = 0; }
+            for (int q = gl; q < 32; q += G) S.hist[q] = 0;
             group_sync<G>(gmask);
             scan_disc<G>(P, g, S, p, i, rho2, step2, true, e, CMAX, gl, gmask, cnt, true);
             group_sync<G>(gmask);
             if (!S.flag) break;
             if (shrink >= 40 || step2 <= rho2 + 1) return CELL_DEFER;
-            step2 = rho2 + (step2 - rho2) / 4;             // too many cutters: a thinner annulus
+            // too many cutters: the annulus up to the last distance bin whose
+            // cutters, with all nearer ones, still fit (a quarter of it when
+            // even the first bin does not fit)
+            const int room = CMAX - C;
+            int b = 0, sum = 0;
+            while (b < 32 && sum + S.hist[b] <= room) sum += S.hist[b++];
+            const i64 width = step2 - rho2;
+            step2 = b > 0 ? rho2 + (i64)((double)width * b / 32.0) : rho2 + width / 4;
+            if (step2 <= rho2) step2 = rho2 + 1;
         }
         rho2 = step2;
         const int ncut = S.ncand - C;
@@ -748,7 +905,8 @@ __device__ int process_cell(const CellParams &P, GroupSmem<CMAX, SMAX, EMAX> &S,
 }
 
 template <int G, int CMAX, int SMAX, int EMAX, int RMAX, bool LARGE>
-__global__ void cells_kernel(CellParams P) {
+__global__ void __launch_bounds__(LARGE ? 32 : 16 * G, (LARGE && CMAX < 1024) ? 21 : 1)
+cells_kernel(CellParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using SM = GroupSmem<CMAX, SMAX, EMAX>;
     if (P.hdr->err) return;

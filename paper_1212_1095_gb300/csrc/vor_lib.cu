@@ -899,6 +899,8 @@ int vor_status(const void *d_workspace, void *stream, vor_stats *stats) {
         stats->evals_first_pass = h.stats[STAT_EVALS1];
         stats->rays_first_pass = h.stats[STAT_RAYS1];
         stats->evals_second_pass = h.stats[STAT_EVALS2];
+        stats->medium_cells = (uint64_t)(h.ndeferred2 > 0 ? h.ndeferred2 : 0);
+        stats->large_cells = (uint64_t)(h.ndeferred3 > 0 ? h.ndeferred3 : 0);
     }
     return map_err(h.err);
 }
