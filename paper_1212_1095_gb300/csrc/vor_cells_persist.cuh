@@ -93,16 +93,23 @@ __global__ void __launch_bounds__(NT) gather_kernel(CellParams P, GatherOut G, f
             const int bx1 = min(g.m1 - 1, (int)floorf(((float)p.x + h) / (float)s));
             if (bx0 > bx1) continue;
             const int a = g.bs[row * g.m1 + bx0], b = g.bs[row * g.m1 + bx1 + 1];
-            for (int pos = a; pos < b; pos++) {
-                if (pos == i) continue;
-                const int2 q = P.sxy[pos];
-                const int nx = q.x - p.x, ny = q.y - p.y;
-                if ((i64)nx * nx + (i64)ny * ny > rho2) continue;
-                if (cnt < GMAX) {
-                    rtab[cnt] = t1::cand_of(nx, ny);
-                    rlab[cnt] = __ldg(P.sid + pos) - g.site_base;
+            // four independent site loads in flight per step
+            for (int pos0 = a; pos0 < b; pos0 += 4) {
+                int2 q[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) q[u] = pos0 + u < b ? __ldg(P.sxy + pos0 + u) : p;
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const int pos = pos0 + u;
+                    if (pos >= b || pos == i) continue;
+                    const int nx = q[u].x - p.x, ny = q[u].y - p.y;
+                    if ((i64)nx * nx + (i64)ny * ny > rho2) continue;
+                    if (cnt < GMAX) {
+                        rtab[cnt] = t1::cand_of(nx, ny);
+                        rlab[cnt] = __ldg(P.sid + pos) - g.site_base;
+                    }
+                    cnt++;
                 }
-                cnt++;
             }
         }
         G.count[t] = cnt > GMAX ? -1 : cnt;

@@ -432,10 +432,18 @@ __device__ __forceinline__ double div_by(double a, double d, double r) {
     return fma(fma(-q, d, a), r, q);
 }
 
-__global__ void k_compact(CompactParams Q) {
+// One thread per cell.  A cell's labels and its neighbours' coordinates are
+// first staged in shared memory with independent loads (the neighbour sites
+// are scattered over the site array), then its vertices are computed.
+constexpr int COMPACT_T = 128;
+
+__global__ void __launch_bounds__(COMPACT_T) k_compact(CompactParams Q) {
+    __shared__ int s_lab[SLOT_CAP][COMPACT_T];
+    __shared__ int2 s_nb[SLOT_CAP][COMPACT_T];
     if (Q.hdr->err) return;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= Q.n) return;
+    const int tid = threadIdx.x;
     const SetMeta &M = set_of(Q.sets, Q.sset, k);
     const int2 *ss = Q.sites + M.site_base;
     const int kl = k - (int)M.site_base;                 // index inside the set
@@ -449,21 +457,45 @@ __global__ void k_compact(CompactParams Q) {
     const int l = Q.loc[k];
     const int *src = l < 0 ? Q.slot + (size_t)k * SLOT_CAP : Q.spill + l;
     const int2 p = Q.sites[k];
-    int lab0 = src[0];
-    int n0x, n0y;
+    const bool staged = e <= SLOT_CAP;
+    if (staged) {
+#pragma unroll
+        for (int q = 0; q < SLOT_CAP; q++)
+            if (q < e) s_lab[q][tid] = __ldg(src + q);
+#pragma unroll
+        for (int q = 0; q < SLOT_CAP; q++) {
+            if (q < e) {
+                const int lab = s_lab[q][tid];
+                s_nb[q][tid] = lab >= 0 ? __ldg(ss + lab) : make_int2(0, 0);
+            }
+        }
+    }
+    // line of the cell's q-th edge: 2 <n, v - p> = c
+    auto line_q = [&](int q, int &lab, int &nx, int &ny, i64 &c) {
+        if (staged) {
+            lab = s_lab[q][tid];
+            if (lab >= 0) {
+                const int2 a = s_nb[q][tid];
+                nx = a.x - p.x;
+                ny = a.y - p.y;
+                c = (i64)nx * nx + (i64)ny * ny;
+                return;
+            }
+        } else {
+            lab = src[q];
+        }
+        line_of(ss, W, H, p, lab, nx, ny, c);
+    };
+    int lab0, n0x, n0y;
     i64 c0;
-    line_of(ss, W, H, p, lab0, n0x, n0y, c0);
+    line_q(0, lab0, n0x, n0y, c0);
     int ax = n0x, ay = n0y, a_lab = lab0;
     i64 ac = c0;
     for (int q = 0; q < e; q++) {
         int bx, by, b_lab;
         i64 bc;
-        if (q + 1 < e) {
-            b_lab = src[q + 1];
-            line_of(ss, W, H, p, b_lab, bx, by, bc);
-        } else {
-            b_lab = lab0; bx = n0x; by = n0y; bc = c0;
-        }
+        if (q + 1 < e) line_q(q + 1, b_lab, bx, by, bc);
+        else { b_lab = lab0; bx = n0x; by = n0y; bc = c0; }
         i64 Nx, Ny, D;
         intersect(ax, ay, ac, bx, by, bc, Nx, Ny, D);
         // absolute vertex (p D + N) / D; the numerators lie in [0, W |D|]
@@ -477,7 +509,7 @@ __global__ void k_compact(CompactParams Q) {
         if (a_lab > kl) {
             int rank = 0;
             for (int r = 0; r < e; r++) {
-                const int o = src[r];
+                const int o = staged ? s_lab[r][tid] : src[r];
                 rank += (o > kl && o < a_lab) ? 1 : 0;
             }
             Q.del_edge[2 * (doff + rank)] = kl;
@@ -544,7 +576,7 @@ static bool resolve(const int64_t *set_ptr, const vor_box *boxes, int n_sets, in
     if (L.n < 0 || L.n > (1 << 27) || L.m_sum > (1ll << 30)) return false;
     L.lanes = o->lanes_per_cell > 0 ? o->lanes_per_cell : 1;
     if (L.lanes != 1 && L.lanes != 2 && L.lanes != 4 && L.lanes != 8 && L.lanes != 16 && L.lanes != 32) return false;
-    L.target = o->target > 0 ? o->target : 22;
+    L.target = o->target > 0 ? o->target : 20;
     if (L.target > 40) return false;
     L.load_pct = o->bucket_load_pct > 0 ? o->bucket_load_pct : 200;
     if (L.load_pct < 25 || L.load_pct > 1600) return false;
@@ -746,7 +778,7 @@ static int launch_build(const BatchArgs &A, const vor_opts *o, void *ws, const L
     Q.cell_ptr = (const long long *)out->cell_ptr; Q.del_ptr = del_ptr;
     Q.edge_label = out->edge_label; Q.vx = out->vx; Q.vy = out->vy; Q.del_edge = out->del_edge;
     Q.edge_cap = out->edge_cap; Q.del_cap = out->del_cap; Q.hdr = hdr;
-    k_compact<<<gn, T, 0, st>>>(Q);
+    k_compact<<<(n + COMPACT_T - 1) / COMPACT_T, COMPACT_T, 0, st>>>(Q);
     launched += 7;                    // 2 x 3 scan kernels, compaction
     if (A.del_set_ptr) {
         k_set_del_ptr<<<(L.n_sets + 1 + T - 1) / T, T, 0, st>>>(sets, L.n_sets, n, del_ptr,
