@@ -410,23 +410,56 @@ __device__ __forceinline__ void line_of(const int2 *set_sites, int W, int H, int
     }
 }
 
-// 1/d for a nonzero integer-valued double |d| < 2^44: a float seed from PTX
-// rcp.approx (relative error below 2^-22 after rounding d to float) refined
-// by two Newton steps in double (error squared each step: below 2^-44, then
-// the rounding of double).
-__device__ __forceinline__ double recip_d(double d) {
-    float r0;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"((float)d));
-    double r = (double)r0;
-    r = fma(r, fma(-d, r, 1.0), r);
-    r = fma(r, fma(-d, r, 1.0), r);
-    return r;
+// float64 values assembled from integer bits (IEEE 754 binary64 layout:
+// sign, 11-bit exponent biased by 1023, 52-bit fraction), so that only the
+// arithmetic proper runs on the float64 pipe.
+
+// an integer v with 0 < v < 2^63, rounded to the nearest double (ties to even)
+__device__ __forceinline__ double u63_to_double_rn(unsigned long long v) {
+    const int e = 63 - __clzll(v);                    // 2^e <= v < 2^(e+1)
+    unsigned long long m;                             // 53 significant bits
+    if (e <= 52) {
+        m = v << (52 - e);
+    } else {
+        const int sh = e - 52;
+        m = v >> sh;
+        const unsigned long long rem = v & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+        if (rem > half || (rem == half && (m & 1))) m++;
+        if (m >> 53) return __longlong_as_double((long long)((unsigned long long)(1023 + e + 1) << 52));
+    }
+    return __longlong_as_double((long long)(((unsigned long long)(1023 + e) << 52) | (m & ((1ull << 52) - 1))));
 }
 
-// a / d from r ~ 1/d: the product, then one correction with its exact
-// residual a - q d (one FMA), which leaves the quotient within half an ulp
-// or so; an exactly representable quotient (an integer vertex) comes out
-// exact.  Well inside the 1e-9 relative tolerance of the vertices.
+// a signed integer |v| < 2^63 to the nearest double
+__device__ __forceinline__ double i63_to_double_rn(long long v) {
+    if (v == 0) return 0.0;
+    const double m = u63_to_double_rn(v < 0 ? (unsigned long long)(-v) : (unsigned long long)v);
+    return v < 0 ? -m : m;
+}
+
+// a normal float, exactly, as a double
+__device__ __forceinline__ double f2d_exact(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+    const unsigned long long ex = (u >> 23) & 0xff, fr = u & 0x7fffff;
+    return __longlong_as_double((long long)(sign | ((ex - 127 + 1023) << 52) | (fr << 29)));
+}
+
+// 1/d for a nonzero integer-valued double |d| < 2^44 (given as the integer
+// D): a float seed from PTX rcp.approx (relative error below 2^-22 after D is
+// rounded to float), widened exactly, then one Newton step in double (error
+// squared: below 2^-44).
+__device__ __forceinline__ double recip_d(long long D, double d) {
+    float r0;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"(__ll2float_rn(D)));
+    const double r = f2d_exact(r0);
+    return fma(r, fma(-d, r, 1.0), r);
+}
+
+// a / d from r ~ 1/d: the product, then one correction with its residual
+// a - q d (one FMA), which leaves the quotient within about half an ulp; an
+// exactly representable quotient (an integer vertex) comes out exact.  Well
+// inside the 1e-9 relative tolerance of the vertices.
 __device__ __forceinline__ double div_by(double a, double d, double r) {
     const double q = a * r;
     return fma(fma(-q, d, a), r, q);
@@ -502,9 +535,9 @@ __global__ void __launch_bounds__(COMPACT_T) k_compact(CompactParams Q) {
         const i64 numx = (i64)((unsigned long long)p.x * (unsigned long long)D + (unsigned long long)Nx);
         const i64 numy = (i64)((unsigned long long)p.y * (unsigned long long)D + (unsigned long long)Ny);
         Q.edge_label[off + q] = a_lab;
-        const double dD = (double)D, rD = recip_d(dD);
-        Q.vx[off + q] = div_by((double)numx, dD, rD);
-        Q.vy[off + q] = div_by((double)numy, dD, rD);
+        const double dD = i63_to_double_rn(D), rD = recip_d(D, dD);   // D exact: |D| < 2^44
+        Q.vx[off + q] = div_by(i63_to_double_rn(numx), dD, rD);
+        Q.vy[off + q] = div_by(i63_to_double_rn(numy), dD, rD);
         // Delaunay pair (k, a) for a > k at rank = number of smaller such labels
         if (a_lab > kl) {
             int rank = 0;
