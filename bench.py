@@ -58,14 +58,20 @@ def parse():
 
 
 def dist_init(args):
+    """One process per GPU (torchrun): NCCL when GPUs are present, gloo on a
+    host without one (the host-side logic is tested that way)."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if ws > 1:
         import torch
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+        if not dist.is_initialized():
+            if torch.cuda.is_available():
+                torch.cuda.set_device(local)
+                dist.init_process_group("nccl")
+            else:
+                dist.init_process_group("gloo")
     return ws, rank, local
 
 
@@ -76,13 +82,21 @@ def barrier(ws):
 
 
 def max_over_ranks(ws, value: float) -> float:
+    """The largest value over the ranks (the slowest rank's time)."""
     if ws == 1:
         return value
     import torch
     import torch.distributed as dist
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def aggregate(ws, units_per_rank: float, seconds: float) -> float:
+    """Whole-job throughput: the units all ranks processed (every rank runs
+    its own replica of the workload) over the slowest rank's time."""
+    return ws * units_per_rank / max_over_ranks(ws, seconds)
 
 
 class Clocks:
