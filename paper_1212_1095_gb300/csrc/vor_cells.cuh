@@ -475,7 +475,9 @@ __device__ int flower_row_spans(const CellGrid &g, const SM &S, int e, int2 p, i
             if (j == j0) { lo[j] = fminf(lo[j], a); hi[j] = fmaxf(hi[j], b); }
     }
     if (nk == 0) return 0;
-    // sort (insertion, K small), then merge overlapping intervals
+    // sort (insertion, K small), then merge overlapping intervals: the
+    // pieces below must come out disjoint and ascending, or a site would be
+    // read (and added) twice
 #pragma unroll
     for (int x = 1; x < K; x++) {
 #pragma unroll
@@ -486,6 +488,27 @@ __device__ int flower_row_spans(const CellGrid &g, const SM &S, int e, int2 p, i
                 lo[y - 1] = tl; hi[y - 1] = th;
             }
         }
+    }
+    {
+        int m = 1;                                       // merged intervals so far
+#pragma unroll
+        for (int j = 1; j < K; j++) {
+            if (j < nk) {
+                float last_hi = hi[0];
+#pragma unroll
+                for (int q = 1; q < K; q++) if (q == m - 1) last_hi = hi[q];
+                if (lo[j] <= last_hi) {
+#pragma unroll
+                    for (int q = 0; q < K; q++) if (q == m - 1) hi[q] = fmaxf(hi[q], hi[j]);
+                } else {
+                    const float a = lo[j], b = hi[j];
+#pragma unroll
+                    for (int q = 1; q < K; q++) if (q == m) { lo[q] = a; hi[q] = b; }
+                    m++;
+                }
+            }
+        }
+        nk = m;
     }
     // the inner disc over the whole band: |dy| is at most dyf there
     const i64 dyf = max(llabs(ylo - p.y), llabs(yhi - p.y));

@@ -92,3 +92,23 @@ def test_batch_4096_sampled_sets():
         s = xy[ptr[j]:ptr[j + 1]]
         mode = "plain" if s.shape[0] <= 2000 else "bucketed"
         assert_full_parity(to_numpy(B.set(j)), oracle.cells(s, BOX, mode))
+
+
+def test_large_clustered_request_with_many_large_cells():
+    # request 842 of the saturated serving stream: 963,722 clustered sites
+    # (a slice of the Gaussian-mixture pool); its cluster-hull cells reach the
+    # large tier, whose row scan once read overlapping ranges twice
+    pools = synth.serve_pools()
+    seed = synth.SEED_BASE + 51
+    _, sizes, kinds = synth.poisson_requests(2000, 100.0, seed=seed)
+    xy = synth.serve_request(842 + seed * 100000, sizes[842], kinds[842], pools)
+    n = xy.shape[0]
+    d = to_numpy(vg.build(torch.from_numpy(xy).cuda(), BOX))
+    e, ext = _cell_extents(d)
+    rng = np.random.default_rng(842)
+    k = np.nonzero((xy[:, 0] == 705893) & (xy[:, 1] == 388283))[0]
+    sel = np.unique(np.concatenate([rng.choice(n, 2000, replace=False), k,
+                                    np.argsort(-ext)[:300], np.argsort(-e)[:50]]))
+    assert_sampled_parity(d, oracle.cells(xy, BOX, "bucketed", sel=sel), sel)
+    area = _areas(d)
+    assert abs(area.sum() - float(BOX) * BOX) <= 1e-8 * float(BOX) * BOX
