@@ -201,6 +201,17 @@ __global__ void __launch_bounds__(NT) cells_persist_kernel(CellParams P, GatherO
                         if (e > 1 && last == first) e--;           // the walk closes
                         if (e < 3) defer = true;
                     }
+                    // the edges' labels, loaded first so that their latency
+                    // overlaps the certificate below (independent loads)
+                    int lq[EMAX];
+                    {
+                        const int *__restrict__ gl = G.lab + (size_t)ctt * G.gmax - 4;
+#pragma unroll
+                        for (int q = 0; q < EMAX; q++) {
+                            const int c = q < e ? emit_get(q) : 0;
+                            lq[q] = (!defer && c >= 4) ? __ldg(gl + c) : -1 - c;
+                        }
+                    }
                     if (!defer) {
                         // security-radius certificate: 2R <= rho
                         float R2 = 0.f;
@@ -211,7 +222,7 @@ __global__ void __launch_bounds__(NT) cells_persist_kernel(CellParams P, GatherO
                             T.line(emit_get(q + 1 < e ? q + 1 : 0), n2x, n2y, c2);
                             intersect(n1x, n1y, c1, n2x, n2y, c2, Nx, Ny, D);
                             if (D == 0) { defer = true; break; }
-                            const float rd = 1.f / (float)D;
+                            const float rd = t1::rcp_approx((float)D);
                             const float vx = (float)Nx * rd, vy = (float)Ny * rd;
                             R2 = fmaxf(R2, fmaf(vx, vx, vy * vy));
                         }
@@ -240,25 +251,14 @@ __global__ void __launch_bounds__(NT) cells_persist_kernel(CellParams P, GatherO
                             dst = P.spill + off;
                         }
                         if (!defer) {
-                            // labels from the gather list, eight independent loads
-                            // at a time
-                            const int *__restrict__ gl = G.lab + (size_t)ctt * G.gmax - 4;
+                            // edge q goes to position (q - start) mod e
                             int dcnt = 0;
-                            for (int q0 = 0; q0 < e; q0 += 8) {
-                                int lq[8];
 #pragma unroll
-                                for (int u = 0; u < 8; u++) {
-                                    int qq = start + q0 + u;
-                                    if (qq >= e) qq -= e;
-                                    const int c = q0 + u < e ? emit_get(qq) : 0;
-                                    lq[u] = c >= 4 ? __ldg(gl + c) : -1 - c;
-                                }
-#pragma unroll
-                                for (int u = 0; u < 8; u++) {
-                                    if (q0 + u < e) {
-                                        dst[q0 + u] = lq[u];
-                                        dcnt += lq[u] > kl ? 1 : 0;
-                                    }
+                            for (int q = 0; q < EMAX; q++) {
+                                if (q < e) {
+                                    const int at = q >= start ? q - start : q - start + e;
+                                    dst[at] = lq[q];
+                                    dcnt += lq[q] > kl ? 1 : 0;
                                 }
                             }
                             P.ecount[k] = e;
@@ -282,8 +282,17 @@ __global__ void __launch_bounds__(NT) cells_persist_kernel(CellParams P, GatherO
                     const int tt = t;
                     i = P.cell_list ? P.cell_list[t] : t;
                     t += stride;
+                    // the whole list row, copied while the count is still on
+                    // its way (entries past the count are never read)
+                    if (tt < G.cap) {
+                        const float2 *src = G.tab + (size_t)tt * G.gmax;
+#pragma unroll 8
+                        for (int q = 0; q < CMAX - 4; q++)
+                            cp_async8(&tbl_raw[(4 + q) * NT + threadIdx.x], src + q);
+                    }
                     const int nc = G.count[tt];
                     if (nc < 0) {                                   // disc too crowded
+                        cp_async_wait_all();      // the table is reused by the next cell
                         if (P.deferred) {
                             const int q = atomicAdd(P.deferred_count, 1);
                             P.deferred[q] = i;
@@ -306,10 +315,6 @@ __global__ void __launch_bounds__(NT) cells_persist_kernel(CellParams P, GatherO
                     T.put(1, t1::cand_of(cW - p.x, 0));
                     T.put(2, t1::cand_of(0, cH - p.y));
                     T.put(3, t1::cand_of(-p.x, 0));
-                    // the candidates: asynchronous 8-byte copies straight into
-                    // the table, all in flight at once
-                    const float2 *src = G.tab + (size_t)tt * G.gmax;
-                    for (int q = 0; q < nc; q++) cp_async8(&tbl_raw[(4 + q) * NT + threadIdx.x], src + q);
                     cp_async_wait_all();
                     ctt = tt;
                     C = nc + 4;
