@@ -51,19 +51,21 @@ struct GatherOut {
 // One thread per cell: the cells are the sorted positions t < P.n, or
 // P.cell_list[t] for t < *P.list_count; outputs are indexed by t.  Each
 // candidate is written in the form the projector's table holds, so loading a
-// cell is a plain copy.  A block stages its cells' lists in shared memory
-// (one padded row per cell) and writes them out as one contiguous range.
-template <int NT, int GMAX>
+// cell is a plain copy.  With STAGE, a block stages its cells' lists in
+// shared memory (one padded row per cell) and writes them out as one
+// contiguous range; without, each thread writes its own row (the second
+// pass, whose longer lists would limit the block to one warp).
+template <int NT, int GMAX, bool STAGE>
 __global__ void __launch_bounds__(NT) gather_kernel(CellParams P, GatherOut G, float target) {
-    __shared__ float2 stab[NT * (GMAX + 1)];
-    __shared__ int slab[NT * (GMAX + 1)];
+    __shared__ float2 stab[STAGE ? NT * (GMAX + 1) : 1];
+    __shared__ int slab[STAGE ? NT * (GMAX + 1) : 1];
     if (P.hdr->err) return;
     const int total = P.cell_list ? *P.list_count : P.n;
     const int t0 = blockIdx.x * NT;
     if (t0 >= total) return;
     const int t = t0 + threadIdx.x;
-    float2 *rtab = stab + threadIdx.x * (GMAX + 1);
-    int *rlab = slab + threadIdx.x * (GMAX + 1);
+    float2 *rtab = STAGE ? stab + threadIdx.x * (GMAX + 1) : G.tab + (size_t)t * GMAX;
+    int *rlab = STAGE ? slab + threadIdx.x * (GMAX + 1) : G.lab + (size_t)t * GMAX;
     if (t < total && t >= G.cap) G.count[t] = -1;
     if (t < total && t < G.cap) {
         const int i = P.cell_list ? P.cell_list[t] : t;
@@ -117,6 +119,7 @@ __global__ void __launch_bounds__(NT) gather_kernel(CellParams P, GatherOut G, f
         G.count[t] = cnt > GMAX ? -1 : cnt;
         G.rho2[t] = rho2;
     }
+    if (!STAGE) return;
     __syncthreads();
     // the block's rows [t0, t0 + rows) are contiguous in the lists
     const int rows = min(min(total, G.cap), t0 + NT) - t0;
