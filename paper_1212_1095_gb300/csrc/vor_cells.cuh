@@ -68,10 +68,11 @@ struct Counters {
 enum { CELL_OK = 0, CELL_DEFER = 1, CELL_FAIL = 2 };
 
 // Float filter: the computed key k of a candidate satisfies
-//   |k - K| <= 6.1 u (|nx||tx| + |ny||ty|) / c,  u = 2^-24
-// (rounding of theta to float, of the dot product and of 1/c).  The kernel
-// uses tol = (|nx|+|ny|)/c * max(|tx|,|ty|) * 2^-19 (= 32 u), a margin of
-// more than 5x, which also absorbs the rounding of k + tol and k - tol.
+//   |k - K| <= 7.1 u (|nx||tx| + |ny||ty|) / c,  u = 2^-24
+// (theta rounded to float u, the dot product 2u, c = nx^2 + ny^2 by one FMA
+// 2u and its rounded reciprocal u, the product u).  The kernel uses
+// tol = (|nx|+|ny|)/c * max(|tx|,|ty|) * 2^-19 (= 32 u), a margin of more
+// than 4x, which also absorbs the rounding of k + tol and k - tol.
 #define VOR_TOL_SCALE 0x1p-19f
 
 struct Filt { float u1, ls, u2, ux; int i1; };
@@ -563,7 +564,7 @@ __device__ int flower_row_spans(const CellGrid &g, const SM &S, int e, int2 p, i
 // exact (the vertex as N/D of its two lines) when the bound cannot decide.
 template <class SM>
 __device__ __forceinline__ bool cuts_polygon(const SM &S, int e, int nx, int ny, i64 cc) {
-    const float fnx = (float)nx, fny = (float)ny, fc = (float)cc;
+    const float fnx = (float)nx, fny = (float)ny, fc = fmaf(fnx, fnx, fny * fny);   // c (2u)
     for (int v = 0; v < e; v++) {
         const float vx = S.vx[v], vy = S.vy[v];
         const float f = 2.f * fmaf(fnx, vx, fny * vy) - fc;
@@ -615,8 +616,8 @@ __device__ int scan_disc(const CellParams &P, const CellGrid &g, GroupSmem<CMAX,
         }
         const int at = atomicAdd(&S.ncand, 1);
         if (at < cap) {
-            const float fc = (float)cc, rc = 1.f / fc;
-            S.cand[at] = make_float4((float)nx, (float)ny, rc, (float)(abs(nx) + abs(ny)) * rc);
+            const float fnx = (float)nx, fny = (float)ny, rc = 1.f / fmaf(fnx, fnx, fny * fny);
+            S.cand[at] = make_float4(fnx, fny, rc, (float)(abs(nx) + abs(ny)) * rc);
             S.lab[at] = P.sid[pos] - g.site_base;
         } else {
             S.flag = 1;

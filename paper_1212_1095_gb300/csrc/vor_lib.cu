@@ -410,59 +410,60 @@ __device__ __forceinline__ void line_of(const int2 *set_sites, int W, int H, int
     }
 }
 
-// float64 values assembled from integer bits (IEEE 754 binary64 layout:
-// sign, 11-bit exponent biased by 1023, 52-bit fraction), so that only the
-// arithmetic proper runs on the float64 pipe.
+// Vertex coordinates without float64 arithmetic (the float64 pipe of this
+// GPU is narrow, and 64-bit integer <-> float conversions issue to it).  A
+// coordinate is the quotient q = num / D of two integers with 0 <= q <= 2^20
+// (the vertex lies in the box), 0 < D < 2^44 and num < 2^63 after taking
+// D's sign into num.  q is computed as a float-float pair (about 44 correct
+// bits, on the FMA pipe), turned into the fixed-point integer F ~ q 2^40,
+// snapped to the exact k 2^40 when the nearest integer k has k D == num, and
+// written as a float64 assembled from F's bits (IEEE 754 binary64: sign,
+// 11-bit exponent biased by 1023, 52-bit fraction).  Error below 2^-42 q +
+// 2^-39, far inside the 1e-9 tolerance of the vertices; integer
+// coordinates are exact.
 
-// an integer v with 0 < v < 2^63, rounded to the nearest double (ties to even)
-__device__ __forceinline__ double u63_to_double_rn(unsigned long long v) {
-    const int e = 63 - __clzll(v);                    // 2^e <= v < 2^(e+1)
-    unsigned long long m;                             // 53 significant bits
-    if (e <= 52) {
-        m = v << (52 - e);
-    } else {
-        const int sh = e - 52;
-        m = v >> sh;
-        const unsigned long long rem = v & ((1ull << sh) - 1), half = 1ull << (sh - 1);
-        if (rem > half || (rem == half && (m & 1))) m++;
-        if (m >> 53) return __longlong_as_double((long long)((unsigned long long)(1023 + e + 1) << 52));
-    }
-    return __longlong_as_double((long long)(((unsigned long long)(1023 + e) << 52) | (m & ((1ull << 52) - 1))));
+// 0 <= v < 2^63 as a float-float pair h + l: h holds v's top 24 bits
+// exactly, l the rest rounded (relative error of h + l below 2^-46)
+__device__ __forceinline__ void u63_to_ff(unsigned long long v, float &h, float &l) {
+    const int top = 63 - __clzll(v);
+    const int sh = top > 23 ? top - 23 : 0;
+    const unsigned hi = (unsigned)(v >> sh);
+    const unsigned long long rem = v - ((unsigned long long)hi << sh);
+    h = (float)hi * __uint_as_float((unsigned)(127 + sh) << 23);      // hi 2^sh, exact
+    l = fmaf((float)(unsigned)(rem >> 32), 4294967296.f, (float)(unsigned)rem);
 }
 
-// a signed integer |v| < 2^63 to the nearest double
-__device__ __forceinline__ double i63_to_double_rn(long long v) {
-    if (v == 0) return 0.0;
-    const double m = u63_to_double_rn(v < 0 ? (unsigned long long)(-v) : (unsigned long long)v);
-    return v < 0 ? -m : m;
+// a / d in float-float, a and d given as float-float pairs, r ~ 1 / dh
+__device__ __forceinline__ void ff_div(float ah, float al, float dh, float dl, float r,
+                                       float &qh, float &ql) {
+    qh = ah * r;
+    const float ph = qh * dh, pl = fmaf(qh, dh, -ph);  // qh dh exactly, as ph + pl
+    const float e = ((ah - ph) - pl) + al - qh * dl;    // a - qh d, to a few ulp of it
+    ql = e * r;
 }
 
-// a normal float, exactly, as a double
-__device__ __forceinline__ double f2d_exact(float f) {
-    const unsigned u = __float_as_uint(f);
-    const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
-    const unsigned long long ex = (u >> 23) & 0xff, fr = u & 0x7fffff;
-    return __longlong_as_double((long long)(sign | ((ex - 127 + 1023) << 52) | (fr << 29)));
+// x 2^40 truncated to an integer, |x| < 2^21
+__device__ __forceinline__ long long f32_fixed40(float x) {
+    const unsigned u = __float_as_uint(x);
+    const int e = (int)((u >> 23) & 0xff) - 110;       // x = m 2^(e - 40), m the 24-bit significand
+    const unsigned long long m = (u & 0x7fffffu) | 0x800000u;
+    const unsigned long long v = e >= 0 ? m << e : (e > -24 ? m >> -e : 0ull);
+    return (u >> 31) ? -(long long)v : (long long)v;
 }
 
-// 1/d for a nonzero integer-valued double |d| < 2^44 (given as the integer
-// D): a float seed from PTX rcp.approx (relative error below 2^-22 after D is
-// rounded to float), widened exactly, then one Newton step in double (error
-// squared: below 2^-44).
-__device__ __forceinline__ double recip_d(long long D, double d) {
-    float r0;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"(__ll2float_rn(D)));
-    const double r = f2d_exact(r0);
-    return fma(r, fma(-d, r, 1.0), r);
-}
-
-// a / d from r ~ 1/d: the product, then one correction with its residual
-// a - q d (one FMA), which leaves the quotient within about half an ulp; an
-// exactly representable quotient (an integer vertex) comes out exact.  Well
-// inside the 1e-9 relative tolerance of the vertices.
-__device__ __forceinline__ double div_by(double a, double d, double r) {
-    const double q = a * r;
-    return fma(fma(-q, d, a), r, q);
+// num / D (D > 0) from the float-float quotient qh + ql, as described above
+__device__ __forceinline__ double vertex_coord(long long num, unsigned long long D, float qh, float ql) {
+    long long F = f32_fixed40(qh) + f32_fixed40(ql);
+    const long long k = (F + (1ll << 39)) >> 40;
+    if (k >= 0 && (unsigned long long)k * D == (unsigned long long)num) F = k << 40;
+    const unsigned long long sgn = F < 0 ? 1ull << 63 : 0ull;
+    const unsigned long long mag = F < 0 ? 0ull - (unsigned long long)F : (unsigned long long)F;
+    if (mag == 0) return 0.0;
+    const int top = 63 - __clzll(mag);                   // 2^top <= mag < 2^61
+    const unsigned long long m = top > 52 ? mag >> (top - 52) : mag << (52 - top);
+    const unsigned long long bits = sgn | ((unsigned long long)(top - 40 + 1023) << 52) |
+                                    (m & ((1ull << 52) - 1));
+    return __longlong_as_double((long long)bits);
 }
 
 // One thread per cell.  A cell's labels and its neighbours' coordinates are
@@ -535,9 +536,18 @@ __global__ void __launch_bounds__(COMPACT_T) k_compact(CompactParams Q) {
         const i64 numx = (i64)((unsigned long long)p.x * (unsigned long long)D + (unsigned long long)Nx);
         const i64 numy = (i64)((unsigned long long)p.y * (unsigned long long)D + (unsigned long long)Ny);
         Q.edge_label[off + q] = a_lab;
-        const double dD = i63_to_double_rn(D), rD = recip_d(D, dD);   // D exact: |D| < 2^44
-        Q.vx[off + q] = div_by(i63_to_double_rn(numx), dD, rD);
-        Q.vy[off + q] = div_by(i63_to_double_rn(numy), dD, rD);
+        // the quotients with D > 0 (numerators >= 0: the vertex is in the box)
+        const unsigned long long aD = D < 0 ? 0ull - (unsigned long long)D : (unsigned long long)D;
+        const long long ax_ = D < 0 ? -numx : numx, ay_ = D < 0 ? -numy : numy;
+        float dh, dl, xh, xl, yh, yl, qh, ql, r;
+        u63_to_ff(aD, dh, dl);
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(dh));
+        u63_to_ff((unsigned long long)ax_, xh, xl);
+        ff_div(xh, xl, dh, dl, r, qh, ql);
+        Q.vx[off + q] = vertex_coord(ax_, aD, qh, ql);
+        u63_to_ff((unsigned long long)ay_, yh, yl);
+        ff_div(yh, yl, dh, dl, r, qh, ql);
+        Q.vy[off + q] = vertex_coord(ay_, aD, qh, ql);
         // Delaunay pair (k, a) for a > k at rank = number of smaller such labels
         if (a_lab > kl) {
             int rank = 0;
