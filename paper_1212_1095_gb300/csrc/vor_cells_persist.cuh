@@ -35,6 +35,10 @@ __device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
 }
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
+}
 __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.wait_all;" ::: "memory");
 }
@@ -46,7 +50,51 @@ struct GatherOut {
     int *lab;          // gmax labels per cell: the site's index in its set
     int gmax;
     int cap;           // cells the lists hold (later cells go to the next pass)
+    // entry q of list row t is at tab[q * cap + t] (entry-major: the rows of
+    // consecutive cells, which one warp loads together, interleave)
 };
+
+// The first disc of the cell of p: the radius rho (squared) for about
+// `target` sites inside, from the site density of the 3x3 buckets around p,
+// and the bucket rows it meets.
+struct Disc {
+    i64 rho2;
+    int r, by0, by1;        // r >= rho + 1, rows by0..by1
+};
+
+__device__ __forceinline__ Disc first_disc(const CellGrid &g, int2 p, float target) {
+    const int s = g.s;
+    const int bx = p.x / s, by = p.y / s;
+    int c9 = 0, nb9 = 0;
+    const int x0 = max(bx - 1, 0), x1 = min(bx + 1, g.m1 - 1);
+    for (int row = max(by - 1, 0); row <= min(by + 1, g.m2 - 1); row++) {
+        c9 += g.bs[row * g.m1 + x1 + 1] - g.bs[row * g.m1 + x0];
+        nb9 += x1 - x0 + 1;
+    }
+    Disc d;
+    const float area = (float)nb9 * (float)s * (float)s;
+    d.rho2 = (i64)(target * area / (3.14159265f * (float)max(c9 - 1, 1)));
+    d.rho2 = max(min(d.rho2, (i64)(16.f * (float)s * (float)s)), (i64)4);
+    d.r = (int)ceilf(sqrtf((float)d.rho2)) + 1;
+    d.by0 = p.y - d.r <= 0 ? 0 : (p.y - d.r) / s;
+    d.by1 = min(g.m2 - 1, (p.y + d.r) / s);
+    return d;
+}
+
+// The buckets bx0..bx1 of bucket row `row` that meet the disc (its chord,
+// widened by one unit); false when none does.  bx0 >= (p.x - r) / s and
+// bx1 <= (p.x + r) / s.
+__device__ __forceinline__ bool chord_cols(const CellGrid &g, int2 p, i64 rho2, int row, int &bx0,
+                                           int &bx1) {
+    const int s = g.s;
+    const i64 ylo = (i64)row * s, yhi = ylo + s;
+    const i64 dy = p.y < ylo ? ylo - p.y : (p.y > yhi ? p.y - yhi : 0);
+    if (dy * dy > rho2) return false;
+    const float h = sqrtf((float)(rho2 - dy * dy)) + 1.f;
+    bx0 = max(0, (int)floorf(((float)p.x - h) / (float)s));
+    bx1 = min(g.m1 - 1, (int)floorf(((float)p.x + h) / (float)s));
+    return bx0 <= bx1;
+}
 
 // One thread per cell: the cells are the sorted positions t < P.n, or
 // P.cell_list[t] for t < *P.list_count; outputs are indexed by t.  Each
@@ -64,38 +112,20 @@ __global__ void __launch_bounds__(NT) gather_kernel(CellParams P, GatherOut G, f
     const int t0 = blockIdx.x * NT;
     if (t0 >= total) return;
     const int t = t0 + threadIdx.x;
-    float2 *rtab = STAGE ? stab + threadIdx.x * (GMAX + 1) : G.tab + (size_t)t * GMAX;
-    int *rlab = STAGE ? slab + threadIdx.x * (GMAX + 1) : G.lab + (size_t)t * GMAX;
+    float2 *rtab = STAGE ? stab + threadIdx.x * (GMAX + 1) : G.tab + t;
+    int *rlab = STAGE ? slab + threadIdx.x * (GMAX + 1) : G.lab + t;
+    const size_t rs = STAGE ? 1 : (size_t)G.cap;          // entry stride of a row
     if (t < total && t >= G.cap) G.count[t] = -1;
     if (t < total && t < G.cap) {
         const int i = P.cell_list ? P.cell_list[t] : t;
         const int2 p = P.sxy[i];
         const CellGrid g = cell_grid(P, i);
-        const int s = g.s;
-        const int bx = p.x / s, by = p.y / s;
-        int c9 = 0, nb9 = 0;
-        {
-            const int x0 = max(bx - 1, 0), x1 = min(bx + 1, g.m1 - 1);
-            for (int row = max(by - 1, 0); row <= min(by + 1, g.m2 - 1); row++) {
-                c9 += g.bs[row * g.m1 + x1 + 1] - g.bs[row * g.m1 + x0];
-                nb9 += x1 - x0 + 1;
-            }
-        }
-        const float area = (float)nb9 * (float)s * (float)s;
-        i64 rho2 = (i64)(target * area / (3.14159265f * (float)max(c9 - 1, 1)));
-        rho2 = max(min(rho2, (i64)(16.f * (float)s * (float)s)), (i64)4);
-        const int r = (int)ceilf(sqrtf((float)rho2)) + 1;
-        const int by0 = p.y - r <= 0 ? 0 : (p.y - r) / s, by1 = min(g.m2 - 1, (p.y + r) / s);
+        const Disc d = first_disc(g, p, target);
+        const i64 rho2 = d.rho2;
         int cnt = 0;
-        for (int row = by0; row <= by1; row++) {
-            // the buckets of this row that meet the disc (its chord, widened)
-            const i64 ylo = (i64)row * s, yhi = ylo + s;
-            const i64 dy = p.y < ylo ? ylo - p.y : (p.y > yhi ? p.y - yhi : 0);
-            if (dy * dy > rho2) continue;
-            const float h = sqrtf((float)(rho2 - dy * dy)) + 1.f;
-            const int bx0 = max(0, (int)floorf(((float)p.x - h) / (float)s));
-            const int bx1 = min(g.m1 - 1, (int)floorf(((float)p.x + h) / (float)s));
-            if (bx0 > bx1) continue;
+        for (int row = d.by0; row <= d.by1; row++) {
+            int bx0, bx1;
+            if (!chord_cols(g, p, rho2, row, bx0, bx1)) continue;
             const int a = g.bs[row * g.m1 + bx0], b = g.bs[row * g.m1 + bx1 + 1];
             // four independent site loads in flight per step
             for (int pos0 = a; pos0 < b; pos0 += 4) {
@@ -109,8 +139,8 @@ __global__ void __launch_bounds__(NT) gather_kernel(CellParams P, GatherOut G, f
                     const int nx = q[u].x - p.x, ny = q[u].y - p.y;
                     if ((i64)nx * nx + (i64)ny * ny > rho2) continue;
                     if (cnt < GMAX) {
-                        rtab[cnt] = t1::cand_of(nx, ny);
-                        rlab[cnt] = __ldg(P.sid + pos) - g.site_base;
+                        rtab[cnt * rs] = t1::cand_of(nx, ny);
+                        rlab[cnt * rs] = __ldg(P.sid + pos) - g.site_base;
                     }
                     cnt++;
                 }
@@ -121,15 +151,190 @@ __global__ void __launch_bounds__(NT) gather_kernel(CellParams P, GatherOut G, f
     }
     if (!STAGE) return;
     __syncthreads();
-    // the block's rows [t0, t0 + rows) are contiguous in the lists
+    // entry q of the block's rows [t0, t0 + rows) is a contiguous range
     const int rows = min(min(total, G.cap), t0 + NT) - t0;
     if (rows <= 0) return;
-    float2 *gt = G.tab + (size_t)t0 * GMAX;
-    int *gl = G.lab + (size_t)t0 * GMAX;
     for (int idx = threadIdx.x; idx < rows * GMAX; idx += NT) {
-        const int rr = idx / GMAX, q = idx - rr * GMAX;
-        gt[idx] = stab[rr * (GMAX + 1) + q];
-        gl[idx] = slab[rr * (GMAX + 1) + q];
+        const int q = idx / rows, rr = idx - q * rows;
+        G.tab[(size_t)q * G.cap + t0 + rr] = stab[rr * (GMAX + 1) + q];
+        G.lab[(size_t)q * G.cap + t0 + rr] = slab[rr * (GMAX + 1) + q];
+    }
+}
+
+// Strip gather (the first pass, which lists every cell): the NT cells of a
+// block are consecutive in sorted order, i.e. mostly neighbours along one
+// bucket row, and their discs overlap.  The block takes its cells in
+// segments of equal (set, bucket row).  For a segment it loads the bucket
+// starts and the sites of the rectangle of buckets that covers the
+// segment's discs into shared memory once (asynchronous copies, mostly from
+// L2); each thread lists its cell's candidates as indices into that copy,
+// and the block then writes the lists entry by entry, every entry q for
+// the segment's consecutive rows at once (whole sectors; rows with fewer
+// entries get padding, which the projector never reads).  A segment whose
+// rectangle does not fit the shared arrays (large discs in sparse regions)
+// lists from global memory and writes its rows directly, like
+// gather_kernel.  The lists and counts are the same as gather_kernel's (the
+// same disc, the same chord buckets, the same order).
+template <int NT, int GMAX, int SCAP, int BCAP, int RCAP>
+__global__ void __launch_bounds__(NT) gather_strip_kernel(CellParams P, GatherOut G, float target) {
+    static_assert(SCAP <= 65536, "shared site indices are 16-bit");
+    __shared__ int2 s_xy[SCAP];
+    __shared__ int s_id[SCAP];
+    __shared__ int s_bs[BCAP];
+    __shared__ unsigned short s_ent[GMAX * NT];        // entry q of thread r: s_ent[q * NT + r]
+    __shared__ int s_roff[RCAP + 1];
+    __shared__ long long s_key[NT];
+    __shared__ int2 s_p[NT];
+    __shared__ int s_cnt[NT];                           // -1: the row was written directly
+    __shared__ int s_box[5];
+    if (P.hdr->err) return;
+    const int total = min(P.n, G.cap);
+    const int t0 = blockIdx.x * NT;
+    if (t0 >= total) return;
+    const int tid = threadIdx.x;
+    const int t = t0 + tid;
+    const bool act = t < total;
+    const int nact = min(NT, total - t0);
+    int2 p = make_int2(0, 0);
+    CellGrid g{};
+    Disc d{};
+    if (act) {
+        p = P.sxy[t];
+        g = cell_grid(P, t);
+        d = first_disc(g, p, target);
+        // segment key: (set, bucket row); non-decreasing along t
+        s_key[tid] = ((long long)(P.sset ? P.sset[t] : 0) << 21) | (p.y / g.s);
+        s_p[tid] = p;
+    }
+    int cnt = 0;
+    // a row from global memory, written directly (rows outside the staged
+    // rectangle; none by construction of the rectangle)
+    auto list_global = [&](int row, int bx0, int bx1) {
+        const int a = g.bs[row * g.m1 + bx0], b = g.bs[row * g.m1 + bx1 + 1];
+        for (int pos0 = a; pos0 < b; pos0 += 4) {
+            int2 q[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) q[u] = pos0 + u < b ? __ldg(P.sxy + pos0 + u) : p;
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int pos = pos0 + u;
+                if (pos >= b || pos == t) continue;
+                const int nx = q[u].x - p.x, ny = q[u].y - p.y;
+                if ((i64)nx * nx + (i64)ny * ny > d.rho2) continue;
+                if (cnt < GMAX) {
+                    G.tab[(size_t)cnt * G.cap + t] = t1::cand_of(nx, ny);
+                    G.lab[(size_t)cnt * G.cap + t] = __ldg(P.sid + pos) - g.site_base;
+                }
+                cnt++;
+            }
+        }
+    };
+    __syncthreads();
+    for (int lo = 0; lo < nact;) {
+        const long long key = s_key[lo];
+        const bool mine = act && s_key[tid] == key;
+        if (tid == 0) { s_box[0] = INT_MAX; s_box[1] = -1; s_box[2] = INT_MAX; s_box[3] = -1; s_box[4] = 0; }
+        __syncthreads();
+        if (mine) {
+            // every chord's buckets lie in these columns: chord_cols' bounds
+            // with the half-width h <= r, the same float operations
+            atomicMin(&s_box[0], d.by0);
+            atomicMax(&s_box[1], d.by1);
+            atomicMin(&s_box[2], max(0, (int)floorf(((float)p.x - (float)d.r) / (float)g.s)));
+            atomicMax(&s_box[3], min(g.m1 - 1, (int)floorf(((float)p.x + (float)d.r) / (float)g.s)));
+        }
+        const int len = __syncthreads_count(mine);     // the segment is threads lo .. lo + len - 1
+        const int R0 = s_box[0], R = s_box[1] - R0 + 1, C0 = s_box[2], C1 = s_box[3] - C0 + 2;
+        bool staged = R <= RCAP && R * C1 <= BCAP;
+        const CellGrid gs = cell_grid(P, t0 + lo);      // the segment's set
+        if (staged) {
+            for (int k = tid; k < R * C1; k += NT) {
+                const int rr = k / C1;
+                cp_async4(s_bs + k, gs.bs + (R0 + rr) * gs.m1 + C0 + (k - rr * C1));
+            }
+            cp_async_wait_all();
+        }
+        __syncthreads();
+        if (staged && tid == 0) {
+            int acc = 0;
+            for (int rr = 0; rr < R; rr++) {
+                s_roff[rr] = acc;
+                acc += s_bs[rr * C1 + C1 - 1] - s_bs[rr * C1];
+            }
+            s_roff[R] = acc;
+        }
+        __syncthreads();
+        staged = staged && s_roff[R] <= SCAP;
+        if (staged) {
+            // the rectangle's sites: row rr's buckets C0 .. C0 + C1 - 2 hold the
+            // sorted positions s_bs[rr * C1] .. s_bs[rr * C1 + C1 - 1] - 1
+            for (int rr = 0; rr < R; rr++) {
+                const int a = s_bs[rr * C1], nr = s_bs[rr * C1 + C1 - 1] - a, o = s_roff[rr];
+                for (int j = tid; j < nr; j += NT) {
+                    cp_async8(s_xy + o + j, P.sxy + a + j);
+                    cp_async4(s_id + o + j, P.sid + a + j);
+                }
+            }
+            cp_async_wait_all();
+        }
+        __syncthreads();
+        if (mine) {
+            bool direct = !staged;
+            for (int row = d.by0; row <= d.by1 && !direct; row++) {
+                int bx0, bx1;
+                if (!chord_cols(g, p, d.rho2, row, bx0, bx1)) continue;
+                if (bx0 < C0 || bx1 + 1 - C0 >= C1) { direct = true; break; }
+                const int *rb = s_bs + (row - R0) * C1;
+                const int a = rb[bx0 - C0], b = rb[bx1 + 1 - C0];
+                const int sb = s_roff[row - R0] - rb[0];        // shared index of position pos: pos + sb
+                for (int pos = a; pos < b; pos++) {
+                    if (pos == t) continue;
+                    const int2 q = s_xy[pos + sb];
+                    const int nx = q.x - p.x, ny = q.y - p.y;
+                    if ((i64)nx * nx + (i64)ny * ny > d.rho2) continue;
+                    if (cnt < GMAX) s_ent[cnt * NT + tid] = (unsigned short)(pos + sb);
+                    cnt++;
+                }
+            }
+            if (direct) {
+                cnt = 0;
+                for (int row = d.by0; row <= d.by1; row++) {
+                    int bx0, bx1;
+                    if (chord_cols(g, p, d.rho2, row, bx0, bx1)) list_global(row, bx0, bx1);
+                }
+                s_cnt[tid] = -1;
+            } else {
+                s_cnt[tid] = cnt;
+                atomicMax(&s_box[4], min(cnt, GMAX));
+            }
+        }
+        __syncthreads();
+        if (staged) {
+            // entry q of the segment's rows: one contiguous range of each list
+            const int M = s_box[4];
+            const int base = gs.site_base;
+            for (int q = 0; q < M; q++) {
+                const int rr = lo + tid;
+                if (tid < len && s_cnt[rr] >= 0) {
+                    float2 v = make_float2(0.f, 0.f);
+                    int lab = -1;
+                    if (q < s_cnt[rr]) {
+                        const int e = s_ent[q * NT + rr];
+                        const int2 a = s_xy[e], pr = s_p[rr];
+                        v = t1::cand_of(a.x - pr.x, a.y - pr.y);
+                        lab = s_id[e] - base;
+                    }
+                    G.tab[(size_t)q * G.cap + t0 + rr] = v;
+                    G.lab[(size_t)q * G.cap + t0 + rr] = lab;
+                }
+            }
+        }
+        __syncthreads();                                 // the shared arrays are reused
+        lo += len;
+    }
+    if (act) {
+        G.count[t] = cnt > GMAX ? -1 : cnt;
+        G.rho2[t] = d.rho2;
     }
 }
 
@@ -210,11 +415,11 @@ __global__ void __launch_bounds__(NT) cells_persist_kernel(CellParams P, GatherO
                     // overlaps the certificate below (independent loads)
                     int lq[EMAX];
                     {
-                        const int *__restrict__ gl = G.lab + (size_t)ctt * G.gmax - 4;
+                        const int *__restrict__ gl = G.lab + ctt;
 #pragma unroll
                         for (int q = 0; q < EMAX; q++) {
                             const int c = q < e ? emit_get(q) : 0;
-                            lq[q] = (!defer && c >= 4) ? __ldg(gl + c) : -1 - c;
+                            lq[q] = (!defer && c >= 4) ? __ldg(gl + (size_t)(c - 4) * G.cap) : -1 - c;
                         }
                     }
                     if (!defer) {
@@ -290,10 +495,10 @@ __global__ void __launch_bounds__(NT) cells_persist_kernel(CellParams P, GatherO
                     // the whole list row, copied while the count is still on
                     // its way (entries past the count are never read)
                     if (tt < G.cap) {
-                        const float2 *src = G.tab + (size_t)tt * G.gmax;
+                        const float2 *src = G.tab + tt;
 #pragma unroll 8
                         for (int q = 0; q < CMAX - 4; q++)
-                            cp_async8(&tbl_raw[(4 + q) * NT + threadIdx.x], src + q);
+                            cp_async8(&tbl_raw[(4 + q) * NT + threadIdx.x], src + (size_t)q * G.cap);
                     }
                     const int nc = G.count[tt];
                     if (nc < 0) {                                   // disc too crowded

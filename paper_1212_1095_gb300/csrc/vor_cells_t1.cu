@@ -16,7 +16,10 @@ cudaError_t launch_gather_pass(const CellParams &P, int pass, int *gcount, long 
                                float2 *gtab, int *glab, cudaStream_t st) {
     const int total_max = P.cell_list ? P.n_list : P.n;
     const GatherOut G = gather_out(P, pass, gcount, grho2, gtab, glab);
-    if (pass == 1)
+    if (pass == 1 && !P.cell_list)
+        gather_strip_kernel<128, P1_CMAX - 4, 1280, 1280, 32><<<(total_max + 127) / 128, 128, 0, st>>>(
+            P, G, (float)P.target);
+    else if (pass == 1)
         gather_kernel<64, P1_CMAX - 4, true><<<(total_max + 63) / 64, 64, 0, st>>>(P, G, (float)P.target);
     else
         gather_kernel<128, P2_CMAX - 4, false><<<(total_max + 127) / 128, 128, 0, st>>>(P, G, 2.2f * (float)P.target);
