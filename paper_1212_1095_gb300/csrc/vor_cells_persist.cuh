@@ -168,9 +168,9 @@ __global__ void __launch_bounds__(NT) gather_kernel(CellParams P, GatherOut G, f
 // starts and the sites of the rectangle of buckets that covers the
 // segment's discs into shared memory once (asynchronous copies, mostly from
 // L2); each thread lists its cell's candidates as indices into that copy,
-// and the block then writes the lists entry by entry, every entry q for
-// the segment's consecutive rows at once (whole sectors; rows with fewer
-// entries get padding, which the projector never reads).  A segment whose
+// then the segment's threads write their rows entry by entry in step, so
+// that entry q of the consecutive rows goes out at once (whole sectors;
+// rows with fewer entries get padding, which the projector never reads).  A segment whose
 // rectangle does not fit the shared arrays (large discs in sparse regions)
 // lists from global memory and writes its rows directly, like
 // gather_kernel.  The lists and counts are the same as gather_kernel's (the
@@ -184,7 +184,6 @@ __global__ void __launch_bounds__(NT) gather_strip_kernel(CellParams P, GatherOu
     __shared__ unsigned short s_ent[GMAX * NT];        // entry q of thread r: s_ent[q * NT + r]
     __shared__ int s_roff[RCAP + 1];
     __shared__ long long s_key[NT];
-    __shared__ int2 s_p[NT];
     __shared__ int s_cnt[NT];                           // -1: the row was written directly
     __shared__ int s_box[5];
     if (P.hdr->err) return;
@@ -204,7 +203,6 @@ __global__ void __launch_bounds__(NT) gather_strip_kernel(CellParams P, GatherOu
         d = first_disc(g, p, target);
         // segment key: (set, bucket row); non-decreasing along t
         s_key[tid] = ((long long)(P.sset ? P.sset[t] : 0) << 21) | (p.y / g.s);
-        s_p[tid] = p;
     }
     int cnt = 0;
     // a row from global memory, written directly (rows outside the staged
@@ -287,14 +285,19 @@ __global__ void __launch_bounds__(NT) gather_strip_kernel(CellParams P, GatherOu
                 const int *rb = s_bs + (row - R0) * C1;
                 const int a = rb[bx0 - C0], b = rb[bx1 + 1 - C0];
                 const int sb = s_roff[row - R0] - rb[0];        // shared index of position pos: pos + sb
-                for (int pos = a; pos < b; pos++) {
-                    if (pos == t) continue;
-                    const int2 q = s_xy[pos + sb];
+                auto take = [&](int pos, int2 q) {
                     const int nx = q.x - p.x, ny = q.y - p.y;
-                    if ((i64)nx * nx + (i64)ny * ny > d.rho2) continue;
+                    if (pos == t || (i64)nx * nx + (i64)ny * ny > d.rho2) return;
                     if (cnt < GMAX) s_ent[cnt * NT + tid] = (unsigned short)(pos + sb);
                     cnt++;
+                };
+                int pos = a;
+                for (; pos + 1 < b; pos += 2) {                  // two sites per step
+                    const int2 q0 = s_xy[pos + sb], q1 = s_xy[pos + 1 + sb];
+                    take(pos, q0);
+                    take(pos + 1, q1);
                 }
+                if (pos < b) take(pos, s_xy[pos + sb]);
             }
             if (direct) {
                 cnt = 0;
@@ -309,24 +312,22 @@ __global__ void __launch_bounds__(NT) gather_strip_kernel(CellParams P, GatherOu
             }
         }
         __syncthreads();
-        if (staged) {
-            // entry q of the segment's rows: one contiguous range of each list
+        if (staged && mine && s_cnt[tid] >= 0) {
+            // the thread writes its own row, entry by entry in step with the
+            // segment's other threads: entry q of consecutive rows is one
+            // contiguous range of each list
             const int M = s_box[4];
-            const int base = gs.site_base;
             for (int q = 0; q < M; q++) {
-                const int rr = lo + tid;
-                if (tid < len && s_cnt[rr] >= 0) {
-                    float2 v = make_float2(0.f, 0.f);
-                    int lab = -1;
-                    if (q < s_cnt[rr]) {
-                        const int e = s_ent[q * NT + rr];
-                        const int2 a = s_xy[e], pr = s_p[rr];
-                        v = t1::cand_of(a.x - pr.x, a.y - pr.y);
-                        lab = s_id[e] - base;
-                    }
-                    G.tab[(size_t)q * G.cap + t0 + rr] = v;
-                    G.lab[(size_t)q * G.cap + t0 + rr] = lab;
+                float2 v = make_float2(0.f, 0.f);
+                int lab = -1;
+                if (q < cnt) {
+                    const int e = s_ent[q * NT + tid];
+                    const int2 a = s_xy[e];
+                    v = t1::cand_of(a.x - p.x, a.y - p.y);
+                    lab = s_id[e] - g.site_base;
                 }
+                G.tab[(size_t)q * G.cap + t] = v;
+                G.lab[(size_t)q * G.cap + t] = lab;
             }
         }
         __syncthreads();                                 // the shared arrays are reused
