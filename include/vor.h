@@ -205,7 +205,7 @@ int vor_stage_ms(float *ms, int max_stages);
  * device array of VOR_NOALLOC_SCRATCH_BYTES (64 MiB) inside the library; it
  * occupies that memory on every GPU where it has been loaded until the
  * process exits.  n must satisfy vor_workspace_bytes(n, box, opts) <=
- * VOR_NOALLOC_SCRATCH_BYTES (up to 101,662 sites in a 2^20 x 2^20 box with the
+ * VOR_NOALLOC_SCRATCH_BYTES (up to 101,656 sites in a 2^20 x 2^20 box with the
  * default options); larger n is rejected with VOR_E_SCRATCH_LIMIT before any
  * work is launched.  No cudaMalloc, cudaFree or other allocating routine is called.
  *

@@ -50,8 +50,14 @@ struct GatherOut {
     int *lab;          // gmax labels per cell: the site's index in its set
     int gmax;
     int cap;           // cells the lists hold (later cells go to the next pass)
-    // entry q of list row t is at tab[q * cap + t] (entry-major: the rows of
-    // consecutive cells, which one warp loads together, interleave)
+    // The rows are stored in tiles of 32 consecutive rows; inside a tile
+    // entry-major, so that entry q of the 32 rows a projector warp loads
+    // together is one contiguous 256-byte range and the warp's whole load
+    // stays inside one tile (a few pages, however many rows there are).
+    // The buffers hold whole tiles.
+    __device__ __forceinline__ size_t at(int t, int q) const {
+        return (size_t)(t >> 5) * ((size_t)gmax * 32) + (size_t)q * 32 + (t & 31);
+    }
 };
 
 // The first disc of the cell of p: the radius rho (squared) for about
@@ -112,9 +118,9 @@ __global__ void __launch_bounds__(NT) gather_kernel(CellParams P, GatherOut G, f
     const int t0 = blockIdx.x * NT;
     if (t0 >= total) return;
     const int t = t0 + threadIdx.x;
-    float2 *rtab = STAGE ? stab + threadIdx.x * (GMAX + 1) : G.tab + t;
-    int *rlab = STAGE ? slab + threadIdx.x * (GMAX + 1) : G.lab + t;
-    const size_t rs = STAGE ? 1 : (size_t)G.cap;          // entry stride of a row
+    float2 *rtab = STAGE ? stab + threadIdx.x * (GMAX + 1) : G.tab + G.at(t, 0);
+    int *rlab = STAGE ? slab + threadIdx.x * (GMAX + 1) : G.lab + G.at(t, 0);
+    const int rs = STAGE ? 1 : 32;                         // entry stride of a row
     if (t < total && t >= G.cap) G.count[t] = -1;
     if (t < total && t < G.cap) {
         const int i = P.cell_list ? P.cell_list[t] : t;
@@ -156,8 +162,8 @@ __global__ void __launch_bounds__(NT) gather_kernel(CellParams P, GatherOut G, f
     if (rows <= 0) return;
     for (int idx = threadIdx.x; idx < rows * GMAX; idx += NT) {
         const int q = idx / rows, rr = idx - q * rows;
-        G.tab[(size_t)q * G.cap + t0 + rr] = stab[rr * (GMAX + 1) + q];
-        G.lab[(size_t)q * G.cap + t0 + rr] = slab[rr * (GMAX + 1) + q];
+        G.tab[G.at(t0 + rr, q)] = stab[rr * (GMAX + 1) + q];
+        G.lab[G.at(t0 + rr, q)] = slab[rr * (GMAX + 1) + q];
     }
 }
 
@@ -220,8 +226,8 @@ __global__ void __launch_bounds__(NT) gather_strip_kernel(CellParams P, GatherOu
                 const int nx = q[u].x - p.x, ny = q[u].y - p.y;
                 if ((i64)nx * nx + (i64)ny * ny > d.rho2) continue;
                 if (cnt < GMAX) {
-                    G.tab[(size_t)cnt * G.cap + t] = t1::cand_of(nx, ny);
-                    G.lab[(size_t)cnt * G.cap + t] = __ldg(P.sid + pos) - g.site_base;
+                    G.tab[G.at(t, cnt)] = t1::cand_of(nx, ny);
+                    G.lab[G.at(t, cnt)] = __ldg(P.sid + pos) - g.site_base;
                 }
                 cnt++;
             }
@@ -326,8 +332,8 @@ __global__ void __launch_bounds__(NT) gather_strip_kernel(CellParams P, GatherOu
                     v = t1::cand_of(a.x - p.x, a.y - p.y);
                     lab = s_id[e] - g.site_base;
                 }
-                G.tab[(size_t)q * G.cap + t] = v;
-                G.lab[(size_t)q * G.cap + t] = lab;
+                G.tab[G.at(t, q)] = v;
+                G.lab[G.at(t, q)] = lab;
             }
         }
         __syncthreads();                                 // the shared arrays are reused
@@ -416,11 +422,11 @@ __global__ void __launch_bounds__(NT) cells_persist_kernel(CellParams P, GatherO
                     // overlaps the certificate below (independent loads)
                     int lq[EMAX];
                     {
-                        const int *__restrict__ gl = G.lab + ctt;
+                        const int *__restrict__ gl = G.lab + G.at(ctt, 0);
 #pragma unroll
                         for (int q = 0; q < EMAX; q++) {
                             const int c = q < e ? emit_get(q) : 0;
-                            lq[q] = (!defer && c >= 4) ? __ldg(gl + (size_t)(c - 4) * G.cap) : -1 - c;
+                            lq[q] = (!defer && c >= 4) ? __ldg(gl + (c - 4) * 32) : -1 - c;
                         }
                     }
                     if (!defer) {
@@ -496,10 +502,10 @@ __global__ void __launch_bounds__(NT) cells_persist_kernel(CellParams P, GatherO
                     // the whole list row, copied while the count is still on
                     // its way (entries past the count are never read)
                     if (tt < G.cap) {
-                        const float2 *src = G.tab + tt;
+                        const float2 *src = G.tab + G.at(tt, 0);
 #pragma unroll 8
                         for (int q = 0; q < CMAX - 4; q++)
-                            cp_async8(&tbl_raw[(4 + q) * NT + threadIdx.x], src + (size_t)q * G.cap);
+                            cp_async8(&tbl_raw[(4 + q) * NT + threadIdx.x], src + q * 32);
                     }
                     const int nc = G.count[tt];
                     if (nc < 0) {                                   // disc too crowded

@@ -5,11 +5,12 @@ namespace vor {
 
 static GatherOut gather_out(const CellParams &P, int pass, int *gcount, long long *grho2,
                             float2 *gtab, int *glab) {
-    // both passes share lists of n * (P1_CMAX - 4) entries; the second pass
-    // lists fewer cells (the deferred ones) with more sites each
-    const long long entries = (long long)P.n * (P1_CMAX - 4);
+    // both passes share lists of gather_rows(n) * (P1_CMAX - 4) entries in
+    // tiles of 32 rows; the second pass lists fewer cells (the deferred ones)
+    // with more sites each
+    const long long entries = gather_rows(P.n) * (P1_CMAX - 4);
     if (pass == 1) return GatherOut{gcount, grho2, gtab, glab, P1_CMAX - 4, P.n};
-    return GatherOut{gcount, grho2, gtab, glab, P2_CMAX - 4, (int)(entries / (P2_CMAX - 4))};
+    return GatherOut{gcount, grho2, gtab, glab, P2_CMAX - 4, (int)(entries / ((P2_CMAX - 4) * 32) * 32)};
 }
 
 cudaError_t launch_gather_pass(const CellParams &P, int pass, int *gcount, long long *grho2,
@@ -49,5 +50,6 @@ cudaError_t launch_cells_pass(const CellParams &P, int pass, int *gcount, long l
 }
 
 int pass_gather_width() { return P1_CMAX - 4; }
+long long gather_rows(long long n) { return (n + 31) / 32 * 32; }
 
 }  // namespace vor

@@ -648,8 +648,8 @@ static bool resolve(const int64_t *set_ptr, const vor_box *boxes, int n_sets, in
     L.deferred3 = at; at = align256(at + nn * 4);
     L.gcount = at;   at = align256(at + nn * 4);
     L.grho2 = at;    at = align256(at + nn * 8);
-    L.gtab = at;     at = align256(at + nn * 8 * (size_t)pass_gather_width());
-    L.glab = at;     at = align256(at + nn * 4 * (size_t)pass_gather_width());
+    L.gtab = at;     at = align256(at + (size_t)gather_rows(nn) * 8 * (size_t)pass_gather_width());
+    L.glab = at;     at = align256(at + (size_t)gather_rows(nn) * 4 * (size_t)pass_gather_width());
     L.coarse = at;   at = align256(at + (size_t)L.g_sum * 4);
     L.total = at;
     return true;
