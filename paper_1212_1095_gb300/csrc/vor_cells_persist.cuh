@@ -395,6 +395,7 @@ __global__ void __launch_bounds__(NT) cells_persist_kernel(CellParams P, GatherO
     int2 p = make_int2(0, 0);
     int cW = 0, cH = 0, cbase = 0;   // the cell's box and the first site of its set
     i64 rho2 = 0;
+    float sbf = 0.f;                 // (1 + 2^-18) / (2 dmin), dmin = p's distance to the box
     int phase = 0, h0c = -1, h0w = -1, h1c = -1, h1w = -1;
     i64 lx = 0, ly = 0;
     int llab = -1, ne = 0, rays = 3, first = -1, last = -1;
@@ -528,6 +529,7 @@ __global__ void __launch_bounds__(NT) cells_persist_kernel(CellParams P, GatherO
                         cH = M.H;
                         cbase = (int)M.site_base;
                     }
+                    sbf = (1.f + 0x1p-18f) / (2.f * (float)min(min(p.x, p.y), min(cW - p.x, cH - p.y)));
                     T.put(0, t1::cand_of(0, -p.y));
                     T.put(1, t1::cand_of(cW - p.x, 0));
                     T.put(2, t1::cand_of(0, cH - p.y));
@@ -611,18 +613,22 @@ __global__ void __launch_bounds__(NT) cells_persist_kernel(CellParams P, GatherO
         const int Cq = query ? C : 0;
         const float fx = (float)tx, fy = (float)ty;
         const float eth = fmaxf(fabsf(fx), fabsf(fy)) * 0x1p-19f;
-        float u1a = -FLT_MAX, u2a = -FLT_MAX, lsa = -FLT_MAX, uxa = -FLT_MAX;
-        float u1b = -FLT_MAX, u2b = -FLT_MAX, lsb = -FLT_MAX, uxb = -FLT_MAX;
-        int i1a = -1, i1b = -1;
-        if (Cq > 0) {                                    // the four sides
-#pragma unroll
-            for (int c = 0; c < 4; c++) {
-                float Ua, La;
-                t1::filter_keys(T.get(c), true, fx, fy, eth, Ua, La);
-                if (Ua > u1a) { u2a = u1a; u1a = Ua; i1a = c; lsa = La; } else u2a = fmaxf(u2a, Ua);
-                if (c != la && c != lb) uxa = fmaxf(uxa, Ua);
-            }
+        // A ray towards u (the vertex of lines la and lb) leaves those two lines
+        // out: their entries read (0, 0) during the pass, which makes both of
+        // their bounds NaN (1/0 times 0), and a NaN neither wins a comparison
+        // nor raises a maximum.  The best remaining upper bound is then the
+        // bound ux of the vertex test.
+        float2 ea = make_float2(0.f, 0.f), eb = ea;
+        if (utest) {
+            ea = T.get(la);
+            eb = T.get(lb);
+            T.put(la, make_float2(0.f, 0.f));
+            T.put(lb, make_float2(0.f, 0.f));
         }
+        // the sites (two streams of candidates)
+        float u1a = -FLT_MAX, u2a = -FLT_MAX, lsa = -FLT_MAX;
+        float u1b = -FLT_MAX, u2b = -FLT_MAX, lsb = -FLT_MAX;
+        int i1a = -1, i1b = -1;
         int c = 4;
         for (; c + 1 < Cq; c += 2) {
             float Ua, La, Ub, Lb;
@@ -630,22 +636,41 @@ __global__ void __launch_bounds__(NT) cells_persist_kernel(CellParams P, GatherO
             t1::filter_keys(T.get(c + 1), false, fx, fy, eth, Ub, Lb);
             if (Ua > u1a) { u2a = u1a; u1a = Ua; i1a = c; lsa = La; } else u2a = fmaxf(u2a, Ua);
             if (Ub > u1b) { u2b = u1b; u1b = Ub; i1b = c + 1; lsb = Lb; } else u2b = fmaxf(u2b, Ub);
-            if (c != la && c != lb) uxa = fmaxf(uxa, Ua);
-            if (c + 1 != la && c + 1 != lb) uxb = fmaxf(uxb, Ub);
         }
         if (c < Cq) {
             float Ua, La;
             t1::filter_keys(T.get(c), false, fx, fy, eth, Ua, La);
             if (Ua > u1a) { u2a = u1a; u1a = Ua; i1a = c; lsa = La; } else u2a = fmaxf(u2a, Ua);
-            if (c != la && c != lb) uxa = fmaxf(uxa, Ua);
         }
         if (!query) continue;
-        float u2, ls, ux = fmaxf(uxa, uxb);
+        float u1, u2, ls;
         int i1;
         if (u1b > u1a || (u1b == u1a && i1b >= 0 && i1b < i1a)) {
-            i1 = i1b; ls = lsb; u2 = fmaxf(fmaxf(u2a, u2b), u1a);
+            i1 = i1b; u1 = u1b; ls = lsb; u2 = fmaxf(fmaxf(u2a, u2b), u1a);
         } else {
-            i1 = i1a; ls = lsa; u2 = fmaxf(fmaxf(u2a, u2b), u1b);
+            i1 = i1a; u1 = u1a; ls = lsa; u2 = fmaxf(fmaxf(u2a, u2b), u1b);
+        }
+        // The four sides of X, only when one of them could reach the best
+        // site: the key of a side at distance d from p is +-t/(2d) for a
+        // component t of theta, at most max(|tx|,|ty|) / (2 dmin) <= sb
+        // (sbf carries a relative margin of 2^-18 over the float roundings).
+        // Otherwise sb stands in for their upper bounds.
+        const float sb = fmaxf(fabsf(fx), fabsf(fy)) * sbf;
+        if (!(sb < ls)) {
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                float U, L;
+                t1::filter_keys(T.get(q), true, fx, fy, eth, U, L);
+                if (U > u1) { u2 = u1; u1 = U; i1 = q; ls = L; } else u2 = fmaxf(u2, U);
+            }
+        } else {
+            u2 = fmaxf(u2, sb);
+            u1 = fmaxf(u1, sb);
+        }
+        const float ux = u1;
+        if (utest) {
+            T.put(la, ea);
+            T.put(lb, eb);
         }
         cnt.evals += C;
 
