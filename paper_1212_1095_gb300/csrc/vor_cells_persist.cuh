@@ -68,6 +68,16 @@ struct Disc {
     int r, by0, by1;        // r >= rho + 1, rows by0..by1
 };
 
+// the rows of the disc of squared radius rho2 around p
+__device__ __forceinline__ Disc disc_of(const CellGrid &g, int2 p, i64 rho2) {
+    Disc d;
+    d.rho2 = rho2;
+    d.r = (int)ceilf(sqrtf((float)d.rho2)) + 1;
+    d.by0 = p.y - d.r <= 0 ? 0 : (p.y - d.r) / g.s;
+    d.by1 = min(g.m2 - 1, (p.y + d.r) / g.s);
+    return d;
+}
+
 __device__ __forceinline__ Disc first_disc(const CellGrid &g, int2 p, float target) {
     const int s = g.s;
     const int bx = p.x / s, by = p.y / s;
@@ -77,14 +87,10 @@ __device__ __forceinline__ Disc first_disc(const CellGrid &g, int2 p, float targ
         c9 += g.bs[row * g.m1 + x1 + 1] - g.bs[row * g.m1 + x0];
         nb9 += x1 - x0 + 1;
     }
-    Disc d;
     const float area = (float)nb9 * (float)s * (float)s;
-    d.rho2 = (i64)(target * area / (3.14159265f * (float)max(c9 - 1, 1)));
-    d.rho2 = max(min(d.rho2, (i64)(16.f * (float)s * (float)s)), (i64)4);
-    d.r = (int)ceilf(sqrtf((float)d.rho2)) + 1;
-    d.by0 = p.y - d.r <= 0 ? 0 : (p.y - d.r) / s;
-    d.by1 = min(g.m2 - 1, (p.y + d.r) / s);
-    return d;
+    i64 rho2 = (i64)(target * area / (3.14159265f * (float)max(c9 - 1, 1)));
+    rho2 = max(min(rho2, (i64)(16.f * (float)s * (float)s)), (i64)4);
+    return disc_of(g, p, rho2);
 }
 
 // The buckets bx0..bx1 of bucket row `row` that meet the disc (its chord,
@@ -126,7 +132,14 @@ __global__ void __launch_bounds__(NT) gather_kernel(CellParams P, GatherOut G, f
         const int i = P.cell_list ? P.cell_list[t] : t;
         const int2 p = P.sxy[i];
         const CellGrid g = cell_grid(P, i);
-        const Disc d = first_disc(g, p, target);
+        Disc d = first_disc(g, p, target);
+        if (P.need_in) {
+            // a cell the first pass could not certify: its polygon, which only
+            // shrinks with more candidates, needs rho^2 >= need; that disc is
+            // taken when it is not much larger than the density-based one
+            const float nf = P.need_in[i];
+            if (nf > 0.f && nf <= 1.5f * (float)d.rho2) d = disc_of(g, p, max((i64)nf, (i64)4));
+        }
         const i64 rho2 = d.rho2;
         int cnt = 0;
         for (int row = d.by0; row <= d.by1; row++) {
@@ -415,6 +428,7 @@ __global__ void __launch_bounds__(NT) cells_persist_kernel(CellParams P, GatherO
                     fin = false;
                     bool defer = !ok;
                     int e = ne;
+                    float needf = 0.f;           // the squared radius a deferred polygon needs
                     if (!defer) {
                         if (e > 1 && last == first) e--;           // the walk closes
                         if (e < 3) defer = true;
@@ -446,7 +460,10 @@ __global__ void __launch_bounds__(NT) cells_persist_kernel(CellParams P, GatherO
                         }
                         const i64 cxf = max(p.x, cW - p.x), cyf = max(p.y, cH - p.y);
                         const i64 need = (i64)(4.f * (R2 * (1.f + 0x1p-12f) + 1.f)) + 1;
-                        if (!(need <= rho2 || rho2 >= cxf * cxf + cyf * cyf)) defer = true;
+                        if (!(need <= rho2 || rho2 >= cxf * cxf + cyf * cyf)) {
+                            defer = true;
+                            needf = __ll2float_ru(need);
+                        }
                     }
                     if (!defer) {
                         // canonical order: start at the smallest normal angle
@@ -489,6 +506,7 @@ __global__ void __launch_bounds__(NT) cells_persist_kernel(CellParams P, GatherO
                         if (P.deferred) {
                             const int q = atomicAdd(P.deferred_count, 1);
                             P.deferred[q] = i;
+                            if (P.need_out) P.need_out[i] = needf;
                             cnt.deferred++;
                         } else {
                             atomicOr(&P.hdr->err, ERRB_CAPACITY);
@@ -514,6 +532,7 @@ __global__ void __launch_bounds__(NT) cells_persist_kernel(CellParams P, GatherO
                         if (P.deferred) {
                             const int q = atomicAdd(P.deferred_count, 1);
                             P.deferred[q] = i;
+                            if (P.need_out) P.need_out[i] = 0.f;
                             cnt.deferred++;
                         } else {
                             atomicOr(&P.hdr->err, ERRB_CAPACITY);

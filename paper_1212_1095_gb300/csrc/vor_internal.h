@@ -125,6 +125,9 @@ struct CellParams {
     int *deferred;          // cells handed to the next pass
     int *deferred_count;    // device counter of that list
     int *next_cell;         // dynamic schedule: next list entry to take (null: stride)
+    float *need_out;        // first pass: per deferred cell (by sorted position) the
+                            // squared disc radius its polygon needs, 0 when unknown
+    const float *need_in;   // second pass: the same, read by its gather
     WsHeader *hdr;
 };
 

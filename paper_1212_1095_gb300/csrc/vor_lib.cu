@@ -633,7 +633,7 @@ static bool resolve(const int64_t *set_ptr, const vor_box *boxes, int n_sets, in
     L.sets = at;     at = align256(at + (size_t)n_sets * sizeof(SetMeta));
     L.sset = at;     at = align256(at + (set_ptr ? nn * 4 : 0));
     L.bstart = at;   at = align256(at + (m + 1) * 4);
-    L.rank = at;     at = align256(at + nn * 4);
+    L.rank = at;     at = align256(at + nn * 4);    // bucket ranks; then the first pass's disc needs
     L.sxy = at;      at = align256(at + nn * 8);
     L.sid = at;      at = align256(at + nn * 4);
     L.partial = at;  at = align256(at + (size_t)L.n_partial * 8);
@@ -769,6 +769,9 @@ static int launch_build(const BatchArgs &A, const vor_opts *o, void *ws, const L
         // (or that exceed its table) go on to the second pass
         P.deferred = deferred;
         P.deferred_count = &hdr->ndeferred;
+        // the bucket ranks are free after bucketing: they carry the first
+        // pass's disc needs to the second pass
+        P.need_out = (float *)rank;
         if (launch_gather_pass(P, 1, gcount, grho2, gtab, glab, st) != cudaSuccess) return VOR_E_CUDA;
         mark(2, st);
         if (launch_cells_pass(P, 1, gcount, grho2, gtab, glab, st) != cudaSuccess) return VOR_E_CUDA;
@@ -780,6 +783,8 @@ static int launch_build(const BatchArgs &A, const vor_opts *o, void *ws, const L
         P2.n_list = n;
         P2.deferred = deferred2;
         P2.deferred_count = &hdr->ndeferred2;
+        P2.need_out = nullptr;
+        P2.need_in = (const float *)rank;
         if (launch_gather_pass(P2, 2, gcount, grho2, gtab, glab, st) != cudaSuccess) return VOR_E_CUDA;
         if (launch_cells_pass(P2, 2, gcount, grho2, gtab, glab, st) != cudaSuccess) return VOR_E_CUDA;
         launched += 4;                // two gathers, two persistent passes
@@ -795,6 +800,8 @@ static int launch_build(const BatchArgs &A, const vor_opts *o, void *ws, const L
     }
     // warp per cell for what is left: medium capacities, then large
     CellParams PM = P;
+    PM.need_out = nullptr;
+    PM.need_in = nullptr;
     PM.cell_list = deferred2;
     PM.list_count = &hdr->ndeferred2;
     PM.n_list = n;
