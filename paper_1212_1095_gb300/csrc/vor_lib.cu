@@ -466,99 +466,173 @@ __device__ __forceinline__ double vertex_coord(long long num, unsigned long long
     return __longlong_as_double((long long)bits);
 }
 
-// One thread per cell.  A cell's labels and its neighbours' coordinates are
-// first staged in shared memory with independent loads (the neighbour sites
-// are scattered over the site array), then its vertices are computed.
-constexpr int COMPACT_T = 128;
+// The line of a side of X for the cell of p (labels -1..-4)
+__device__ __forceinline__ void side_line(int W, int H, int2 p, int lab, int &nx, int &ny, i64 &c) {
+    nx = ny = 0;
+    if (lab == VOR_SIDE_BOTTOM) ny = -p.y;
+    else if (lab == VOR_SIDE_RIGHT) nx = W - p.x;
+    else if (lab == VOR_SIDE_TOP) ny = H - p.y;
+    else nx = -p.x;
+    c = 2 * ((i64)nx * nx + (i64)ny * ny);
+}
+
+// The vertex between edge q (line a, label a_lab) and edge q + 1 (line b) of
+// the cell of p, its label, and the Delaunay pair (kl, a_lab) when a_lab > kl,
+// at rank = the number of the cell's labels between kl and a_lab (labs[0..e))
+__device__ __forceinline__ void emit_vertex(const CompactParams &Q, int2 p, int kl, long long off,
+                                            long long doff, const int *labs, int e, int q, int a_lab,
+                                            int ax, int ay, i64 ac, int bx, int by, i64 bc) {
+    i64 Nx, Ny, D;
+    intersect(ax, ay, ac, bx, by, bc, Nx, Ny, D);
+    // absolute vertex (p D + N) / D; the numerators lie in [0, W |D|]
+    const i64 numx = (i64)((unsigned long long)p.x * (unsigned long long)D + (unsigned long long)Nx);
+    const i64 numy = (i64)((unsigned long long)p.y * (unsigned long long)D + (unsigned long long)Ny);
+    Q.edge_label[off + q] = a_lab;
+    // the quotients with D > 0 (numerators >= 0: the vertex is in the box)
+    const unsigned long long aD = D < 0 ? 0ull - (unsigned long long)D : (unsigned long long)D;
+    const long long ax_ = D < 0 ? -numx : numx, ay_ = D < 0 ? -numy : numy;
+    float dh, dl, xh, xl, yh, yl, qh, ql, r;
+    u63_to_ff(aD, dh, dl);
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(dh));
+    u63_to_ff((unsigned long long)ax_, xh, xl);
+    ff_div(xh, xl, dh, dl, r, qh, ql);
+    Q.vx[off + q] = vertex_coord(ax_, aD, qh, ql);
+    u63_to_ff((unsigned long long)ay_, yh, yl);
+    ff_div(yh, yl, dh, dl, r, qh, ql);
+    Q.vy[off + q] = vertex_coord(ay_, aD, qh, ql);
+    if (a_lab > kl) {
+        int rank = 0;
+        for (int j = 0; j < e; j++) {
+            const int o = labs[j];
+            rank += (o > kl && o < a_lab) ? 1 : 0;
+        }
+        Q.del_edge[2 * (doff + rank)] = kl;
+        Q.del_edge[2 * (doff + rank) + 1] = a_lab;
+    }
+}
+
+// A warp takes 32 consecutive cells.  Their labels and neighbour sites are
+// staged in shared memory (one entry per edge, the cells' edges end to end
+// after a prefix sum of e_k over the lanes), and then every lane computes
+// one vertex at a time, whatever cell it belongs to: the lanes stay busy
+// however the cells' edge counts differ.  A warp whose cells have more
+// edges than its staging area lists each cell on one lane from global memory.
+constexpr int COMPACT_W = 4;                 // warps per block
+constexpr int COMPACT_T = 32 * COMPACT_W;
+constexpr int COMPACT_V = 32 * SLOT_CAP;     // staged edges per warp
+
+struct CompactCell {
+    const int *src;                          // the cell's labels (fixed slot or spill)
+    int2 p;
+    int W, H, kl, e, start;                  // kl: the cell's index in its set
+    long long off, doff;                     // first edge, first Delaunay pair
+};
 
 __global__ void __launch_bounds__(COMPACT_T) k_compact(CompactParams Q) {
-    __shared__ int s_lab[SLOT_CAP][COMPACT_T];
-    __shared__ int2 s_nb[SLOT_CAP][COMPACT_T];
+    __shared__ int s_lab[COMPACT_W][COMPACT_V];
+    __shared__ int2 s_nb[COMPACT_W][COMPACT_V];
+    __shared__ CompactCell s_cell[COMPACT_W][32];
     if (Q.hdr->err) return;
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= Q.n) return;
-    const int tid = threadIdx.x;
-    const SetMeta &M = set_of(Q.sets, Q.sset, k);
-    const int2 *ss = Q.sites + M.site_base;
-    const int kl = k - (int)M.site_base;                 // index inside the set
-    const int W = M.W, H = M.H;
-    const int e = Q.ecount[k];
-    const long long off = Q.cell_ptr[k], doff = Q.del_ptr[k];
-    if (off + e > Q.edge_cap || doff + Q.dcount[k] > Q.del_cap) {
-        atomicOr(&Q.hdr->err, ERRB_SPILL);
+    const unsigned FULL = 0xffffffffu;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int k0 = (blockIdx.x * COMPACT_W + w) * 32;
+    if (k0 >= Q.n) return;                                   // warp-uniform
+    const int k = k0 + lane;
+    CompactCell ci{};
+    const int2 *ss = Q.sites;
+    if (k < Q.n) {
+        const SetMeta &M = set_of(Q.sets, Q.sset, k);
+        ss = Q.sites + M.site_base;
+        ci.p = Q.sites[k];
+        ci.W = M.W;
+        ci.H = M.H;
+        ci.kl = k - (int)M.site_base;
+        ci.e = Q.ecount[k];
+        ci.off = Q.cell_ptr[k];
+        ci.doff = Q.del_ptr[k];
+        const int l = Q.loc[k];
+        ci.src = l < 0 ? Q.slot + (size_t)k * SLOT_CAP : Q.spill + l;
+        if (ci.off + ci.e > Q.edge_cap || ci.doff + Q.dcount[k] > Q.del_cap) {
+            atomicOr(&Q.hdr->err, ERRB_SPILL);
+            ci.e = 0;
+        }
+    }
+    // the cells' edges end to end: an inclusive prefix sum over the lanes
+    int incl = ci.e;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const int V = __shfl_sync(FULL, incl, 31);
+    ci.start = incl - ci.e;
+    if (V > COMPACT_V) {
+        // more edges than the staging area: each lane its own cell
+        for (int q = 0; q < ci.e; q++) {
+            int a_lab, ax, ay, b_lab, bx, by;
+            i64 ac, bc;
+            a_lab = ci.src[q];
+            b_lab = ci.src[q + 1 < ci.e ? q + 1 : 0];
+            line_of(ss, ci.W, ci.H, ci.p, a_lab, ax, ay, ac);
+            line_of(ss, ci.W, ci.H, ci.p, b_lab, bx, by, bc);
+            emit_vertex(Q, ci.p, ci.kl, ci.off, ci.doff, ci.src, ci.e, q, a_lab, ax, ay, ac, bx, by, bc);
+        }
         return;
     }
-    const int l = Q.loc[k];
-    const int *src = l < 0 ? Q.slot + (size_t)k * SLOT_CAP : Q.spill + l;
-    const int2 p = Q.sites[k];
-    const bool staged = e <= SLOT_CAP;
-    if (staged) {
+    s_cell[w][lane] = ci;
+    __syncwarp();
+    // the cell (lane) that owns edge v: the first lane with incl > v
+    auto owner = [&](int v) {
+        int lo = 0;
 #pragma unroll
-        for (int q = 0; q < SLOT_CAP; q++)
-            if (q < e) s_lab[q][tid] = __ldg(src + q);
-#pragma unroll
-        for (int q = 0; q < SLOT_CAP; q++) {
-            if (q < e) {
-                const int lab = s_lab[q][tid];
-                s_nb[q][tid] = lab >= 0 ? __ldg(ss + lab) : make_int2(0, 0);
-            }
+        for (int step = 16; step > 0; step >>= 1) {
+            const int x = __shfl_sync(FULL, incl, lo + step - 1);
+            if (x <= v) lo += step;
+        }
+        return lo;
+    };
+    int *lab_w = s_lab[w];
+    int2 *nb_w = s_nb[w];
+    for (int v0 = 0; v0 < V; v0 += 32) {                    // stage labels and neighbour sites
+        const int v = v0 + lane;
+        const int c = owner(min(v, V - 1));
+        if (v < V) {
+            const CompactCell &cc = s_cell[w][c];
+            const int lab = __ldg(cc.src + (v - cc.start));
+            lab_w[v] = lab;
+            nb_w[v] = lab >= 0 ? __ldg(Q.sites + (k0 + c - cc.kl) + lab) : make_int2(0, 0);
         }
     }
-    // line of the cell's q-th edge: 2 <n, v - p> = c
-    auto line_q = [&](int q, int &lab, int &nx, int &ny, i64 &c) {
-        if (staged) {
-            lab = s_lab[q][tid];
-            if (lab >= 0) {
-                const int2 a = s_nb[q][tid];
-                nx = a.x - p.x;
-                ny = a.y - p.y;
-                c = (i64)nx * nx + (i64)ny * ny;
-                return;
+    __syncwarp();
+    for (int v0 = 0; v0 < V; v0 += 32) {                    // one vertex per lane
+        const int v = v0 + lane;
+        const int c = owner(min(v, V - 1));
+        if (v < V) {
+            const CompactCell &cc = s_cell[w][c];
+            const int q = v - cc.start;
+            const int vb = q + 1 < cc.e ? v + 1 : cc.start;
+            const int a_lab = lab_w[v], b_lab = lab_w[vb];
+            int ax, ay, bx, by;
+            i64 ac, bc;
+            if (a_lab >= 0) {
+                const int2 a = nb_w[v];
+                ax = a.x - cc.p.x;
+                ay = a.y - cc.p.y;
+                ac = (i64)ax * ax + (i64)ay * ay;
+            } else {
+                side_line(cc.W, cc.H, cc.p, a_lab, ax, ay, ac);
             }
-        } else {
-            lab = src[q];
-        }
-        line_of(ss, W, H, p, lab, nx, ny, c);
-    };
-    int lab0, n0x, n0y;
-    i64 c0;
-    line_q(0, lab0, n0x, n0y, c0);
-    int ax = n0x, ay = n0y, a_lab = lab0;
-    i64 ac = c0;
-    for (int q = 0; q < e; q++) {
-        int bx, by, b_lab;
-        i64 bc;
-        if (q + 1 < e) line_q(q + 1, b_lab, bx, by, bc);
-        else { b_lab = lab0; bx = n0x; by = n0y; bc = c0; }
-        i64 Nx, Ny, D;
-        intersect(ax, ay, ac, bx, by, bc, Nx, Ny, D);
-        // absolute vertex (p D + N) / D; the numerators lie in [0, W |D|]
-        const i64 numx = (i64)((unsigned long long)p.x * (unsigned long long)D + (unsigned long long)Nx);
-        const i64 numy = (i64)((unsigned long long)p.y * (unsigned long long)D + (unsigned long long)Ny);
-        Q.edge_label[off + q] = a_lab;
-        // the quotients with D > 0 (numerators >= 0: the vertex is in the box)
-        const unsigned long long aD = D < 0 ? 0ull - (unsigned long long)D : (unsigned long long)D;
-        const long long ax_ = D < 0 ? -numx : numx, ay_ = D < 0 ? -numy : numy;
-        float dh, dl, xh, xl, yh, yl, qh, ql, r;
-        u63_to_ff(aD, dh, dl);
-        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(dh));
-        u63_to_ff((unsigned long long)ax_, xh, xl);
-        ff_div(xh, xl, dh, dl, r, qh, ql);
-        Q.vx[off + q] = vertex_coord(ax_, aD, qh, ql);
-        u63_to_ff((unsigned long long)ay_, yh, yl);
-        ff_div(yh, yl, dh, dl, r, qh, ql);
-        Q.vy[off + q] = vertex_coord(ay_, aD, qh, ql);
-        // Delaunay pair (k, a) for a > k at rank = number of smaller such labels
-        if (a_lab > kl) {
-            int rank = 0;
-            for (int r = 0; r < e; r++) {
-                const int o = staged ? s_lab[r][tid] : src[r];
-                rank += (o > kl && o < a_lab) ? 1 : 0;
+            if (b_lab >= 0) {
+                const int2 b = nb_w[vb];
+                bx = b.x - cc.p.x;
+                by = b.y - cc.p.y;
+                bc = (i64)bx * bx + (i64)by * by;
+            } else {
+                side_line(cc.W, cc.H, cc.p, b_lab, bx, by, bc);
             }
-            Q.del_edge[2 * (doff + rank)] = kl;
-            Q.del_edge[2 * (doff + rank) + 1] = a_lab;
+            emit_vertex(Q, cc.p, cc.kl, cc.off, cc.doff, lab_w + cc.start, cc.e, q, a_lab, ax, ay, ac, bx,
+                        by, bc);
         }
-        ax = bx; ay = by; ac = bc; a_lab = b_lab;
     }
 }
 
@@ -828,7 +902,7 @@ static int launch_build(const BatchArgs &A, const vor_opts *o, void *ws, const L
     Q.cell_ptr = (const long long *)out->cell_ptr; Q.del_ptr = del_ptr;
     Q.edge_label = out->edge_label; Q.vx = out->vx; Q.vy = out->vy; Q.del_edge = out->del_edge;
     Q.edge_cap = out->edge_cap; Q.del_cap = out->del_cap; Q.hdr = hdr;
-    k_compact<<<(n + COMPACT_T - 1) / COMPACT_T, COMPACT_T, 0, st>>>(Q);
+    k_compact<<<(n + COMPACT_T - 1) / COMPACT_T, COMPACT_T, 0, st>>>(Q);   // a warp per 32 cells
     launched += 7;                    // 2 x 3 scan kernels, compaction
     if (A.del_set_ptr) {
         k_set_del_ptr<<<(L.n_sets + 1 + T - 1) / T, T, 0, st>>>(sets, L.n_sets, n, del_ptr,
