@@ -84,7 +84,9 @@ __global__ void k_probe_count(const int2 *__restrict__ sites, int n, const SetMe
     const SetMeta &M = set_of(sets, sset, i);
     const int2 p = sites[i];
     if (outside(p, M)) return;                              // reported by k_bucket_count
-    const int cx = (int)((long long)p.x * M.G / M.W), cy = (int)((long long)p.y * M.G / M.H);
+    // 0 <= p < W <= 2^20 and G <= 1024: the products fit 32 bits
+    const int cx = (int)((unsigned)p.x * (unsigned)M.G / (unsigned)M.W);
+    const int cy = (int)((unsigned)p.y * (unsigned)M.G / (unsigned)M.H);
     atomicAdd(&coarse[M.coarse_base + (long long)cy * M.G + cx], 1);
 }
 
@@ -102,7 +104,8 @@ __global__ void k_probe_mean(const int2 *__restrict__ sites, int n, SetMeta *__r
         const SetMeta &M = sets[j];
         const int2 p = sites[i];
         if (!outside(p, M)) {
-            const int cx = (int)((long long)p.x * M.G / M.W), cy = (int)((long long)p.y * M.G / M.H);
+            const int cx = (int)((unsigned)p.x * (unsigned)M.G / (unsigned)M.W);
+            const int cy = (int)((unsigned)p.y * (unsigned)M.G / (unsigned)M.H);
             v = log2f((float)max(coarse[M.coarse_base + (long long)cy * M.G + cx], 1));
         }
     }
@@ -179,7 +182,10 @@ __global__ void k_dup_check(const int2 *__restrict__ sxy, int n, const SetMeta *
 }
 
 // ---------------------------------------------------------------------------
-// exclusive scan (reduce -> scan of block sums -> downsweep)
+// exclusive scan: block totals, then a downsweep; the downsweep sums the
+// preceding block totals itself when there are few blocks (quadratic in
+// the block count, but one launch less), else a one-block scan of the
+// totals runs in between
 // ---------------------------------------------------------------------------
 
 constexpr int SCAN_T = 256, SCAN_I = 8, SCAN_TILE = SCAN_T * SCAN_I;
@@ -241,11 +247,14 @@ __global__ void k_scan_partials(T *__restrict__ partial, int nb, const WsHeader 
     }
 }
 
+constexpr int SCAN_SELF_MAX = 4096;      // block counts up to which the downsweep sums the totals
+
 // out[i] = sum of in[0..i) for i < n, and out[n] = total; optionally *tot = total.
+// partial: with self_carry the blocks' totals, else their exclusive prefix.
 template <class T>
 __global__ void k_scan_down(const int *__restrict__ in, int n, const int *n_dev,
                             const T *__restrict__ partial, T *__restrict__ out, long long *tot,
-                            const WsHeader *hdr) {
+                            bool self_carry, const WsHeader *hdr) {
     __shared__ T sh[32];
     if (hdr->err) return;
     if (n_dev) n = min(n, *n_dev);
@@ -257,29 +266,41 @@ __global__ void k_scan_down(const int *__restrict__ in, int n, const int *n_dev,
         v[q] = (base + q < n) ? (T)in[base + q] : T(0);
         s += v[q];
     }
+    T carry;
+    if (self_carry) {
+        // the totals of the blocks before this one (fewer than SCAN_SELF_MAX)
+        T before = 0;
+        for (int b = threadIdx.x; b < (int)blockIdx.x; b += SCAN_T) before += partial[b];
+        block_exclusive<T>(before, sh, carry);
+    } else {
+        carry = partial[blockIdx.x];
+    }
     T total;
-    T run = partial[blockIdx.x] + block_exclusive<T>(s, sh, total);
+    T run = carry + block_exclusive<T>(s, sh, total);
 #pragma unroll
     for (int q = 0; q < SCAN_I; q++) {
         if (base + q < n) out[base + q] = run;
         run += v[q];
     }
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
-        const T t = partial[blockIdx.x] + total;
+        const T t = carry + total;
         out[n] = t;
         if (tot) *tot = (long long)t;
     }
 }
 
 // Exclusive scan of in[0..n) (n = min(n_max, *n_dev) when n_dev is given).
+// Returns the number of kernels launched.
 template <class T>
-static void scan(const int *in, int n_max, const int *n_dev, T *out, T *partial, long long *tot,
-                 WsHeader *hdr, cudaStream_t st) {
+static int scan(const int *in, int n_max, const int *n_dev, T *out, T *partial, long long *tot,
+                WsHeader *hdr, cudaStream_t st) {
     const int nb = (n_max + SCAN_TILE - 1) / SCAN_TILE;
     const int nbb = nb > 0 ? nb : 1;
+    const bool self_carry = nbb <= SCAN_SELF_MAX;
     k_scan_reduce<T><<<nbb, SCAN_T, 0, st>>>(in, n_max, n_dev, partial, hdr);
-    k_scan_partials<T><<<1, SCAN_T, 0, st>>>(partial, nbb, hdr);
-    k_scan_down<T><<<nbb, SCAN_T, 0, st>>>(in, n_max, n_dev, partial, out, tot, hdr);
+    if (!self_carry) k_scan_partials<T><<<1, SCAN_T, 0, st>>>(partial, nbb, hdr);
+    k_scan_down<T><<<nbb, SCAN_T, 0, st>>>(in, n_max, n_dev, partial, out, tot, self_carry, hdr);
+    return self_carry ? 2 : 3;
 }
 
 // ---------------------------------------------------------------------------
@@ -815,9 +836,9 @@ static int launch_build(const BatchArgs &A, const vor_opts *o, void *ws, const L
     }
     k_pick_grid<<<1, SCAN_T, 0, st>>>(sets, L.n_sets, L.s_fixed, hdr);
     k_bucket_count<<<gn, T, 0, st>>>(sites, n, sets, sset, bstart, rank, hdr);
-    scan<int>(bstart, (int)L.m_sum, &hdr->m_total, bstart, (int *)partial, nullptr, hdr, st);
+    launched += scan<int>(bstart, (int)L.m_sum, &hdr->m_total, bstart, (int *)partial, nullptr, hdr, st);
     k_bucket_scatter<<<gn, T, 0, st>>>(sites, n, sets, sset, bstart, rank, sxy, sid, hdr);
-    launched += 6;                    // pick, count, 3 scan kernels, scatter
+    launched += 3;                    // pick, count, scatter
     if (o->check_duplicates) {
         k_dup_check<<<gn, T, 0, st>>>(sxy, n, sets, sset, bstart, hdr);
         launched++;
@@ -893,9 +914,9 @@ static int launch_build(const BatchArgs &A, const vor_opts *o, void *ws, const L
     launched += 2;
     mark(5, st);
 
-    scan<long long>(ecount, n, nullptr, (long long *)out->cell_ptr, partial, (long long *)out->totals,
-                    hdr, st);
-    scan<long long>(dcount, n, nullptr, del_ptr, partial, (long long *)out->totals + 1, hdr, st);
+    launched += scan<long long>(ecount, n, nullptr, (long long *)out->cell_ptr, partial,
+                                (long long *)out->totals, hdr, st);
+    launched += scan<long long>(dcount, n, nullptr, del_ptr, partial, (long long *)out->totals + 1, hdr, st);
     CompactParams Q;
     Q.sites = sites; Q.n = n; Q.sets = sets; Q.sset = sset;
     Q.ecount = ecount; Q.dcount = dcount; Q.loc = loc; Q.slot = slot; Q.spill = spill;
@@ -903,7 +924,7 @@ static int launch_build(const BatchArgs &A, const vor_opts *o, void *ws, const L
     Q.edge_label = out->edge_label; Q.vx = out->vx; Q.vy = out->vy; Q.del_edge = out->del_edge;
     Q.edge_cap = out->edge_cap; Q.del_cap = out->del_cap; Q.hdr = hdr;
     k_compact<<<(n + COMPACT_T - 1) / COMPACT_T, COMPACT_T, 0, st>>>(Q);   // a warp per 32 cells
-    launched += 7;                    // 2 x 3 scan kernels, compaction
+    launched += 1;                    // compaction
     if (A.del_set_ptr) {
         k_set_del_ptr<<<(L.n_sets + 1 + T - 1) / T, T, 0, st>>>(sets, L.n_sets, n, del_ptr,
                                                                  A.del_set_ptr, hdr);
