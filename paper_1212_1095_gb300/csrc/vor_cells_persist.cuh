@@ -513,7 +513,16 @@ __global__ void __launch_bounds__(NT) cells_persist_kernel(CellParams P, GatherO
                         }
                     }
                 }
-                // load the next cell of this thread's sequence
+                // load the next cell: with a dynamic schedule the idle lanes take
+                // consecutive entries with one atomic (the warp's generation),
+                // else the thread's own sequence t, t + stride, ...
+                if (P.next_cell) {
+                    const int lane = threadIdx.x & 31, leader = __ffs(idlem) - 1;
+                    int base = 0;
+                    if (lane == leader) base = atomicAdd(P.next_cell, __popc(idlem));
+                    base = __shfl_sync(idlem, base, leader);
+                    t = base + __popc(idlem & ((1u << lane) - 1));
+                }
                 while (t < total) {
                     const int tt = t;
                     i = P.cell_list ? P.cell_list[t] : t;
@@ -537,6 +546,7 @@ __global__ void __launch_bounds__(NT) cells_persist_kernel(CellParams P, GatherO
                         } else {
                             atomicOr(&P.hdr->err, ERRB_CAPACITY);
                         }
+                        if (P.next_cell) t = atomicAdd(P.next_cell, 1);
                         continue;
                     }
                     p = P.sxy[i];

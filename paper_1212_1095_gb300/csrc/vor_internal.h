@@ -36,7 +36,8 @@ struct WsHeader {
     int m_total;            // buckets over all sets (set by the grid choice)
     int ndeferred3;         // cells handed from the medium to the large tier
     int large_next2;        // next cell of the large tier
-    long long pad[10];
+    int pass_next[2];       // next list entry of the two thread-per-cell passes
+    long long pad[9];
 };
 static_assert(sizeof(WsHeader) <= 256, "header");
 

@@ -869,7 +869,9 @@ static int launch_build(const BatchArgs &A, const vor_opts *o, void *ws, const L
         P.need_out = (float *)rank;
         if (launch_gather_pass(P, 1, gcount, grho2, gtab, glab, st) != cudaSuccess) return VOR_E_CUDA;
         mark(2, st);
-        if (launch_cells_pass(P, 1, gcount, grho2, gtab, glab, st) != cudaSuccess) return VOR_E_CUDA;
+        CellParams P1 = P;
+        P1.next_cell = &hdr->pass_next[0];          // cells by warp generations from a counter
+        if (launch_cells_pass(P1, 1, gcount, grho2, gtab, glab, st) != cudaSuccess) return VOR_E_CUDA;
         mark(3, st);
         // second pass: a disc with about 2.2 times the sites
         CellParams P2 = P;
@@ -881,6 +883,7 @@ static int launch_build(const BatchArgs &A, const vor_opts *o, void *ws, const L
         P2.need_out = nullptr;
         P2.need_in = (const float *)rank;
         if (launch_gather_pass(P2, 2, gcount, grho2, gtab, glab, st) != cudaSuccess) return VOR_E_CUDA;
+        P2.next_cell = &hdr->pass_next[1];
         if (launch_cells_pass(P2, 2, gcount, grho2, gtab, glab, st) != cudaSuccess) return VOR_E_CUDA;
         launched += 4;                // two gathers, two persistent passes
         mark(4, st);
