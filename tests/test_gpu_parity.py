@@ -87,6 +87,22 @@ def test_clustered_medium():
     assert_full_parity(d, r)
 
 
+def test_cells_with_hundreds_of_edges():
+    # three hubs (indices 0..2), each ringed by 200 sites: every hub's cell is
+    # a 200-gon, so the first 32 cells hold 745 edges, more than one warp of
+    # the compaction stages (512); those cells go through its per-lane path
+    # after the medium and large tiers
+    pts = [[200000, 500000], [500000, 500000], [800000, 500000]]
+    for cx, cy in list(pts):
+        a = 2 * np.pi * (np.arange(200) + 0.25) / 200
+        ring = np.stack([np.rint(cx + 20000 * np.cos(a)), np.rint(cy + 20000 * np.sin(a))], 1)
+        pts += ring.astype(np.int64).tolist()
+    xy = np.array(pts, dtype=np.int32)
+    r = oracle.cells(xy, BOX, "plain")
+    assert np.diff(r["cell_ptr"])[:3].tolist() == [200, 200, 200]
+    assert_full_parity(gpu(xy, BOX), r)
+
+
 def test_errors_are_reported():
     with pytest.raises(vg.VorError) as e:
         gpu(np.array([[0, 5], [3, 4]]), 100)
