@@ -132,39 +132,57 @@ __global__ void __launch_bounds__(NT) gather_kernel(CellParams P, GatherOut G, f
         const int i = P.cell_list ? P.cell_list[t] : t;
         const int2 p = P.sxy[i];
         const CellGrid g = cell_grid(P, i);
-        Disc d = first_disc(g, p, target);
+        const Disc rule = first_disc(g, p, target);
+        Disc d = rule;
         if (P.need_in) {
-            // a cell the first pass could not certify: its polygon, which only
-            // shrinks with more candidates, needs rho^2 >= need; that disc is
-            // taken when it is not much larger than the density-based one
+            // A cell the first pass could not certify: its polygon, which only
+            // shrinks with more candidates, needs rho^2 >= need.  That disc is
+            // taken when it is not much larger than the density-based one, or
+            // else tried first when it is at least 16 times larger (in area)
+            // and spans at most 64 bucket rows (the hull cells of small
+            // clusters: a large disc over mostly empty space), with the
+            // density-based disc as the fallback when it overflows the list.
             const float nf = P.need_in[i];
-            if (nf > 0.f && nf <= 1.5f * (float)d.rho2) d = disc_of(g, p, max((i64)nf, (i64)4));
-        }
-        const i64 rho2 = d.rho2;
-        int cnt = 0;
-        for (int row = d.by0; row <= d.by1; row++) {
-            int bx0, bx1;
-            if (!chord_cols(g, p, rho2, row, bx0, bx1)) continue;
-            const int a = g.bs[row * g.m1 + bx0], b = g.bs[row * g.m1 + bx1 + 1];
-            // four independent site loads in flight per step
-            for (int pos0 = a; pos0 < b; pos0 += 4) {
-                int2 q[4];
-#pragma unroll
-                for (int u = 0; u < 4; u++) q[u] = pos0 + u < b ? __ldg(P.sxy + pos0 + u) : p;
-#pragma unroll
-                for (int u = 0; u < 4; u++) {
-                    const int pos = pos0 + u;
-                    if (pos >= b || pos == i) continue;
-                    const int nx = q[u].x - p.x, ny = q[u].y - p.y;
-                    if ((i64)nx * nx + (i64)ny * ny > rho2) continue;
-                    if (cnt < GMAX) {
-                        rtab[cnt * rs] = t1::cand_of(nx, ny);
-                        rlab[cnt * rs] = __ldg(P.sid + pos) - g.site_base;
-                    }
-                    cnt++;
-                }
+            if (nf > 0.f) {
+                const Disc dn = disc_of(g, p, max((i64)nf, (i64)4));
+                if (nf <= 1.5f * (float)rule.rho2 || (nf >= 16.f * (float)rule.rho2 && dn.by1 - dn.by0 < 64))
+                    d = dn;
             }
         }
+        int cnt = 0;
+        auto list = [&](const Disc &dd) {
+            const i64 rho2 = dd.rho2;
+            cnt = 0;
+            for (int row = dd.by0; row <= dd.by1 && cnt <= GMAX; row++) {
+                int bx0, bx1;
+                if (!chord_cols(g, p, rho2, row, bx0, bx1)) continue;
+                const int a = g.bs[row * g.m1 + bx0], b = g.bs[row * g.m1 + bx1 + 1];
+                // four independent site loads in flight per step
+                for (int pos0 = a; pos0 < b; pos0 += 4) {
+                    int2 q[4];
+#pragma unroll
+                    for (int u = 0; u < 4; u++) q[u] = pos0 + u < b ? __ldg(P.sxy + pos0 + u) : p;
+#pragma unroll
+                    for (int u = 0; u < 4; u++) {
+                        const int pos = pos0 + u;
+                        if (pos >= b || pos == i) continue;
+                        const int nx = q[u].x - p.x, ny = q[u].y - p.y;
+                        if ((i64)nx * nx + (i64)ny * ny > rho2) continue;
+                        if (cnt < GMAX) {
+                            rtab[cnt * rs] = t1::cand_of(nx, ny);
+                            rlab[cnt * rs] = __ldg(P.sid + pos) - g.site_base;
+                        }
+                        cnt++;
+                    }
+                }
+            }
+        };
+        list(d);
+        if (cnt > GMAX && d.rho2 > rule.rho2) {          // the need disc overflowed
+            d = rule;
+            list(d);
+        }
+        const i64 rho2 = d.rho2;
         G.count[t] = cnt > GMAX ? -1 : cnt;
         G.rho2[t] = rho2;
     }
