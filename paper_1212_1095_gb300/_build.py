@@ -45,12 +45,14 @@ def _fingerprint() -> str:
 
 def kernel_fingerprint(names) -> str:
     """Hash of the named csrc files and the compile flags: identifies the code
-    of one kernel (its translation unit and the headers it includes)."""
+    of one kernel (its translation unit and the headers it includes).  The
+    include directories are left out, so the hash is the same wherever the
+    repository sits."""
     h = hashlib.sha256()
     for name in sorted(names):
         with open(os.path.join(CSRC, name), "rb") as f:
             h.update(name.encode() + f.read())
-    h.update(" ".join(ARCH + FLAGS).encode())
+    h.update(" ".join(ARCH + [f for f in FLAGS if not f.startswith("-I")]).encode())
     return h.hexdigest()
 
 
