@@ -89,3 +89,16 @@ def test_batch_sizing_and_autotune_grid_on_the_host(lib):
     for g in grid:
         assert vg.vor_batch_workspace_bytes(ptr, boxes, g) > 0
     assert vg.vor_kernel_launches() >= 0
+
+
+def test_kernel_fingerprint_does_not_depend_on_the_checkout_path(monkeypatch):
+    # bench.py matches committed ncu traffic to the profiled kernel's sources
+    # through this hash; it must be the same wherever the repository sits
+    from paper_1212_1095_gb300 import _build
+    names = ["vor_cells_persist.cuh", "vor_internal.h"]
+    h = _build.kernel_fingerprint(names)
+    moved = [f if not f.startswith("-I") else "-I/elsewhere" + f[2:] for f in _build.FLAGS]
+    monkeypatch.setattr(_build, "FLAGS", moved)
+    assert _build.kernel_fingerprint(names) == h
+    monkeypatch.setattr(_build, "FLAGS", moved + ["-DSOMETHING_ELSE"])
+    assert _build.kernel_fingerprint(names) != h
