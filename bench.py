@@ -56,6 +56,10 @@ def parse():
     ap.add_argument("--batch-steps", type=int, default=5)
     ap.add_argument("--requests", type=int, default=2000,
                     help="serving: requests per measured stream")
+    ap.add_argument("--no-gauss", action="store_true",
+                    help="leave the clustered 4M block out of the default line")
+    ap.add_argument("--no-serve", action="store_true",
+                    help="leave the serving block out of the default line")
     return ap.parse_args()
 
 
@@ -203,6 +207,61 @@ def cpu_baseline(xy, seconds_target: float = 15.0):
     return {"value": len(sel) / dt, "unit": "cells/s", "cores": cores, "kind": "oracle",
             "sample": f"{len(sel)} of {n} cells (stride {stride}), bucketed oracle "
                       f"(Method A.6), {cores} threads, {dt:.1f} s"}
+
+
+def single_block(dev, workload: str, steps: int, warmup: int, ws_n: int = 1) -> dict:
+    """Device time of whole builds of one workload (inputs resident, L2
+    flushed between steps), with the stage times and the counters of one
+    extra build; the filter-failure rate is the share of rays and vertex
+    tests the float filter could not decide (exact int128 fallback)."""
+    import torch
+
+    import paper_1212_1095_gb300 as vg
+    import synth
+
+    xy = synth.workload(workload)
+    n = xy.shape[0]
+    d_sites = torch.from_numpy(xy).to(dev)
+    stream = torch.cuda.current_stream()
+    Ws = vg.Workspace(n, BOX, vg.vor_opts_default(collect_stats=1), device=dev)
+    Ws.launch(d_sites)
+    stats = Ws.finish().stats
+    n_edges, n_del = int(Ws.totals[0].item()), int(Ws.totals[1].item())
+    del Ws
+    torch.cuda.empty_cache()
+    W = vg.Workspace(n, BOX, vg.vor_opts_default(), device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    vg.vor_stage_timing(True)
+    for _ in range(warmup):
+        W.launch(d_sites)
+        W.finish()
+    torch.cuda.synchronize()
+    barrier(ws_n)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    step_ms, stage_acc = [], []
+    for _ in range(steps):
+        flush.fill_(1)
+        e0.record(stream)
+        W.launch(d_sites, stream)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        stage_acc.append(vg.vor_stage_ms())
+    vg.vor_stage_timing(False)
+    rc, _ = vg.vor_status(W.ws_ptr, stream.cuda_stream)
+    if rc != 0:
+        raise vg.VorError(rc, f"{workload} builds")
+    del W, d_sites, flush
+    torch.cuda.empty_cache()
+    ms = max_over_ranks(ws_n, statistics.mean(step_ms))
+    decided = stats["rays"] + stats["vertex_tests"]
+    return {"workload": workload, "n_sites": n, "steps": steps, "warmup": warmup,
+            "ms_per_build": ms, "cells_per_s": ws_n * n / (ms / 1000.0),
+            "stages_ms": {k: statistics.mean(x[i] for x in stage_acc)
+                          for i, k in enumerate(vg.STAGES)},
+            "filter_failure_rate": stats["exact_rays"] / max(decided, 1),
+            "edges": n_edges, "delaunay_edges": n_del, "stats": stats}
 
 
 def run_reference(args):
@@ -524,17 +583,22 @@ def _serve_stream(vg, reqs, arrivals, cfg_kw, pools):
             "mean_wave_requests": float(np.mean(waves)), "waves": st["waves"]}
 
 
-def run_serve(args):
+SERVER_OURS = dict(device_bytes=48 << 30, host_bytes=8 << 30, max_inflight=4,
+                   max_wave_requests=64, max_wave_sites=8 << 20)
+SERVER_PLAIN = dict(device_bytes=48 << 30, host_bytes=8 << 30, max_inflight=1,
+                    max_wave_requests=1, max_wave_sites=8 << 20)
+
+
+def serve_measure(args, local: int) -> dict:
+    """Serving: a saturated burst (every request submitted at once) gives the
+    saturated rate; then Poisson streams at 0.5x and 0.8x of it.  Each stream
+    runs on the continuous-batching server and on the same server limited to
+    one request per wave and one wave at a time (a one-at-a-time FIFO)."""
     import numpy as np
-    import torch
 
     import paper_1212_1095_gb300 as vg
     import synth
 
-    ws_n = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
     pools = synth.serve_pools()
     n_req = args.requests
 
@@ -544,10 +608,7 @@ def run_serve(args):
                 for j, (s, k) in enumerate(zip(sizes, kinds))]
         return arr, reqs
 
-    ours = dict(device_bytes=48 << 30, host_bytes=8 << 30, max_inflight=4,
-                max_wave_requests=64, max_wave_sites=8 << 20)
-    plain = dict(device_bytes=48 << 30, host_bytes=8 << 30, max_inflight=1,
-                 max_wave_requests=1, max_wave_sites=8 << 20)
+    ours, plain = SERVER_OURS, SERVER_PLAIN
     # warm-up (builds the library's launch shapes, pages the pools in)
     _, wreqs = make(100.0, synth.SEED_BASE + 50)
     _serve_stream(vg, wreqs[:max(8, args.warmup * 4)], None, ours, pools)
@@ -566,12 +627,30 @@ def run_serve(args):
         rates.append({"fraction_of_saturation": frac, "rate_rps": rate, "ours": r_ours,
                       "plain": r_plain})
     clk = clocks.stop()
+    mean_size = float(np.mean([s for s, _, _ in sreqs]))
+    return {"requests_per_stream": n_req, "mean_sites": mean_size,
+            "warmup_requests": max(8, args.warmup * 4),
+            "saturated": {"ours": sat, "plain": sat_plain,
+                          "sites_per_s": sat["throughput_rps"] * mean_size,
+                          "speedup_vs_plain": sat["throughput_rps"] / sat_plain["throughput_rps"]},
+            "poisson": rates, "clocks": clk}
+
+
+def run_serve(args):
+    import torch
+
+    ws_n = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    r = serve_measure(args, local)
     if rank != 0:
         return 0
-    mean_size = float(np.mean([s for s, _, _ in sreqs]))
+    n_req, mean_size, sat = r["requests_per_stream"], r["mean_sites"], r["saturated"]["ours"]
+    ours, plain = SERVER_OURS, SERVER_PLAIN
     line = {
         "metric": METRIC, "value": sat["throughput_rps"] * ws_n, "unit": "requests/s",
-        "n_gpus": ws_n, "steps": n_req, "warmup": max(8, args.warmup * 4),
+        "n_gpus": ws_n, "steps": n_req, "warmup": r["warmup_requests"],
         "ms_per_step": 1000.0 * sat["makespan_s"] / n_req, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
         "config": {"workload": "serve", "requests_per_stream": n_req,
@@ -580,10 +659,9 @@ def run_serve(args):
                                    "of 2^21-site pools)",
                    "box": BOX, "server": ours, "plain_server": plain,
                    "parallelism": "1 GPU"},
-        "saturated": {"ours": sat, "plain": sat_plain,
-                      "sites_per_s": sat["throughput_rps"] * mean_size},
-        "poisson": rates,
-        "clocks": clk,
+        "saturated": r["saturated"],
+        "poisson": r["poisson"],
+        "clocks": r["clocks"],
         "e2e": {"value": sat["throughput_rps"] * ws_n, "unit": "requests/s",
                 "h2d_bytes_per_step": int(8 * mean_size),
                 "d2h_bytes_per_step": None,
@@ -745,11 +823,16 @@ def run_ours(args):
                    "one_caller": e2e}
         del callers
 
-    b = None
-    if args.workload == "uniform_1m" and not args.no_batch:
+    b = gb = sv = None
+    if args.workload == "uniform_1m":
         del W
         torch.cuda.empty_cache()
-        b = batch_measure(args, dev, args.batch_steps, 3, ws_n)
+        if not args.no_batch:
+            b = batch_measure(args, dev, args.batch_steps, 3, ws_n)
+        if not args.no_gauss:
+            gb = single_block(dev, "gauss_4m", min(args.steps, 10), 3, ws_n)
+        if not args.no_serve and ws_n == 1:
+            sv = serve_measure(args, local)
     if rank != 0:
         return 0
     # roofline of the projector kernel: plain ALU work (no tensor cores, the
@@ -792,6 +875,10 @@ def run_ours(args):
         line["batched"] = {k: b[k] for k in ("value", "unit", "ms_per_step", "n_sets", "n_sites",
                                             "latency_ms", "plain", "speedup_vs_plain", "opts",
                                             "graph", "stages_ms", "e2e")}
+    if gb is not None:
+        line["gauss_4m"] = gb
+    if sv is not None:
+        line["serve"] = sv
     print(json.dumps(line))
     return 0
 

@@ -152,8 +152,9 @@ int vor_build_async(const vor_site *d_sites, int64_t n, vor_box box, const vor_o
                     void *d_workspace, int64_t ws_bytes, const vor_out *out, void *stream);
 
 /* Status of the last vor_build_async that used this workspace: VOR_OK or a
- * device-detected error.  Synchronises the stream, then reads 4 bytes from
- * the workspace.  stats (may be NULL) receives the counters. */
+ * device-detected error.  Copies the workspace's 256-byte header to the host
+ * on the stream and waits for that stream only (no device-wide
+ * synchronisation).  stats (may be NULL) receives the counters. */
 int vor_status(const void *d_workspace, void *stream, vor_stats *stats);
 
 /* Synchronous convenience form: allocates workspace and worst-case output
@@ -209,9 +210,12 @@ int vor_stage_ms(float *ms, int max_stages);
  * default options); larger n is rejected with VOR_E_SCRATCH_LIMIT before any
  * work is launched.  No cudaMalloc, cudaFree or other allocating routine is called.
  *
- * The first call on a device looks up the array's device address with
- * cudaGetSymbolAddress (with that device current) and caches it; make that
- * first call before any stream capture.  Every call shares the one array,
+ * Every call looks up the array's device address with cudaGetSymbolAddress
+ * in the context current on the calling thread (an address is valid only in
+ * its context; after cudaDeviceReset the array is loaded again elsewhere).
+ * The first call in a context may load the library's module that holds the
+ * array, which reserves its memory: make that first call before any stream
+ * capture.  Every call shares the one array,
  * and the build clears on the stream what must start at zero, so calls that
  * overlap on the GPU (on different streams or from different threads) race
  * and corrupt each other: serialise them.
@@ -358,6 +362,17 @@ int vor_server_statistics(vor_server *s, vor_server_stats *st);
 double vor_server_now(const vor_server *s);
 /* Stops the dispatcher after the running waves, frees everything. */
 int vor_server_destroy(vor_server *s);
+
+/* The vertex-coordinate conversion of the compaction kernel on its own:
+ * d_out[i] = d_num[i] / d_den[i] in float64 for n pairs (device arrays).
+ * A vertex of a cell is stored as p + N / D with exact integers (Section 5
+ * stores vertices; the meeting point of two lines of Section 3); the
+ * library writes its float64 coordinate as this quotient of two integers.
+ * Domain: 0 <= num < 2^63, 0 < den < 2^44, num / den < 2^21; outside it
+ * the result is NaN.  Error at most 2^-42 q + 2^-39 for the exact quotient
+ * q, and integer quotients are exact.  Asynchronous on the stream. */
+int vor_vertex_quotients(const int64_t *d_num, const uint64_t *d_den, int64_t n, double *d_out,
+                         void *stream);
 
 /* Number of kernels this library has launched in this process (all builds,
  * all devices; a captured CUDA graph's replays are not counted). */

@@ -25,7 +25,7 @@ __all__ = ["VorOpts", "VorStats", "VorOut", "VorError", "build_library", "librar
            "vor_stage_ms", "STAGES", "build", "build_host", "Diagram", "vor_batch_edge_capacity",
            "vor_batch_delaunay_capacity", "vor_batch_workspace_bytes", "vor_build_batch_async",
            "BatchWorkspace", "BatchDiagram", "build_batch", "vor_kernel_launches",
-           "vor_autotune_grid", "autotune_batch", "Server", "VorServerConfig",
+           "vor_autotune_grid", "autotune_batch", "Server", "VorServerConfig", "vor_vertex_quotients",
            "vor_server_config_default",
            "SIDE_BOTTOM", "SIDE_RIGHT", "SIDE_TOP", "SIDE_LEFT"]
 
@@ -177,6 +177,8 @@ def library():
     lib.vor_server_now.restype = ctypes.c_double
     lib.vor_server_destroy.argtypes = [P]
     lib.vor_server_destroy.restype = i32
+    lib.vor_vertex_quotients.argtypes = [P, P, i64, P, P]
+    lib.vor_vertex_quotients.restype = i32
     lib.vor_kernel_launches.argtypes = []
     lib.vor_kernel_launches.restype = i64
     lib.vor_strerror.argtypes = [i32]
@@ -235,6 +237,20 @@ def vor_status(ws_ptr: int, stream: int) -> tuple[int, VorStats]:
 
 def vor_host_scratch_bytes(n: int) -> int:
     return int(library().vor_host_scratch_bytes(int(n)))
+
+
+def vor_vertex_quotients(num, den):
+    """num / den in float64 by the library's vertex conversion (torch int64
+    tensors on the GPU of equal length; den holds unsigned values < 2^44)."""
+    import torch
+    out = torch.empty(num.shape[0], dtype=torch.float64, device=num.device)
+    rc = library().vor_vertex_quotients(ctypes.c_void_p(num.data_ptr()),
+                                        ctypes.c_void_p(den.data_ptr()), int(num.shape[0]),
+                                        ctypes.c_void_p(out.data_ptr()),
+                                        ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if rc != 0:
+        raise VorError(rc, "vor_vertex_quotients")
+    return out
 
 
 def vor_kernel_launches() -> int:

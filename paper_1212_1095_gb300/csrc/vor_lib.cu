@@ -441,7 +441,16 @@ __device__ __forceinline__ void line_of(const int2 *set_sites, int W, int H, int
 // written as a float64 assembled from F's bits (IEEE 754 binary64: sign,
 // 11-bit exponent biased by 1023, 52-bit fraction).  Error below 2^-42 q +
 // 2^-39, far inside the 1e-9 tolerance of the vertices; integer
-// coordinates are exact.
+// coordinates are exact (tests/test_gpu_vertex_quotient.py checks both at
+// the extremes through vor_vertex_quotients).
+//
+// The quotient of two float-float numbers is the double-length division of
+// T. J. Dekker, "A floating-point technique for extending the available
+// precision", Numer. Math. 18 (1971): a first quotient qh, the residual
+// a - qh d, and one correction term.  The product qh dh is formed exactly
+// as ph + pl with one fused multiply-add (the FMA form of Dekker's exact
+// product, "TwoProductFMA" in Ogita, Rump and Oishi, "Accurate sum and dot
+// product", SIAM J. Sci. Comput. 26 (2005)).
 
 // 0 <= v < 2^63 as a float-float pair h + l: h holds v's top 24 bits
 // exactly, l the rest rounded (relative error of h + l below 2^-46)
@@ -487,6 +496,40 @@ __device__ __forceinline__ double vertex_coord(long long num, unsigned long long
     return __longlong_as_double((long long)bits);
 }
 
+// num / D for 0 <= num < 2^63, 0 < D < 2^44, num < 2^21 D: the float-float
+// denominator (with the approximate reciprocal of its head) is shared by the
+// two coordinates of a vertex
+struct FFDen { float h, l, r; };
+
+__device__ __forceinline__ FFDen ff_den(unsigned long long D) {
+    FFDen d;
+    u63_to_ff(D, d.h, d.l);
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(d.r) : "f"(d.h));
+    return d;
+}
+
+__device__ __forceinline__ double ff_quotient(long long num, unsigned long long D, const FFDen &d) {
+    float xh, xl, qh, ql;
+    u63_to_ff((unsigned long long)num, xh, xl);
+    ff_div(xh, xl, d.h, d.l, d.r, qh, ql);
+    return vertex_coord(num, D, qh, ql);
+}
+
+__global__ void k_vertex_quotients(const long long *__restrict__ num,
+                                   const unsigned long long *__restrict__ den, long long n,
+                                   double *__restrict__ out) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const long long a = num[i];
+    const unsigned long long D = den[i];
+    // outside the domain of the conversion: NaN
+    if (a < 0 || D == 0 || D >= (1ull << 44) || (unsigned long long)a / D >= (1ull << 21)) {
+        out[i] = __longlong_as_double(0x7ff8000000000000ll);
+        return;
+    }
+    out[i] = ff_quotient(a, D, ff_den(D));
+}
+
 // The line of a side of X for the cell of p (labels -1..-4)
 __device__ __forceinline__ void side_line(int W, int H, int2 p, int lab, int &nx, int &ny, i64 &c) {
     nx = ny = 0;
@@ -512,15 +555,9 @@ __device__ __forceinline__ void emit_vertex(const CompactParams &Q, int2 p, int 
     // the quotients with D > 0 (numerators >= 0: the vertex is in the box)
     const unsigned long long aD = D < 0 ? 0ull - (unsigned long long)D : (unsigned long long)D;
     const long long ax_ = D < 0 ? -numx : numx, ay_ = D < 0 ? -numy : numy;
-    float dh, dl, xh, xl, yh, yl, qh, ql, r;
-    u63_to_ff(aD, dh, dl);
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(dh));
-    u63_to_ff((unsigned long long)ax_, xh, xl);
-    ff_div(xh, xl, dh, dl, r, qh, ql);
-    Q.vx[off + q] = vertex_coord(ax_, aD, qh, ql);
-    u63_to_ff((unsigned long long)ay_, yh, yl);
-    ff_div(yh, yl, dh, dl, r, qh, ql);
-    Q.vy[off + q] = vertex_coord(ay_, aD, qh, ql);
+    const FFDen fd = ff_den(aD);
+    Q.vx[off + q] = ff_quotient(ax_, aD, fd);
+    Q.vy[off + q] = ff_quotient(ay_, aD, fd);
     if (a_lab > kl) {
         int rank = 0;
         for (int j = 0; j < e; j++) {
@@ -1062,8 +1099,11 @@ int vor_build_batch_async(const vor_site *d_sites, const int64_t *d_set_ptr,
 int vor_status(const void *d_workspace, void *stream, vor_stats *stats) {
     if (!d_workspace) return VOR_E_INVALID_ARG;
     WsHeader h;
-    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return VOR_E_CUDA;
-    if (cudaMemcpy(&h, d_workspace, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return VOR_E_CUDA;
+    // ordered on the caller's stream only (no device-wide synchronisation)
+    const cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(&h, d_workspace, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return VOR_E_CUDA;
     if (stats) {
         memset(stats, 0, sizeof(*stats));
         stats->rays = h.stats[STAT_RAYS];
@@ -1213,6 +1253,17 @@ int vor_stage_ms(float *ms, int max_stages) {
 }
 
 int64_t vor_kernel_launches(void) { return (int64_t)g_launches.load(); }
+
+int vor_vertex_quotients(const int64_t *d_num, const uint64_t *d_den, int64_t n, double *d_out,
+                         void *stream) {
+    if (n < 0 || (n > 0 && (!d_num || !d_den || !d_out))) return VOR_E_INVALID_ARG;
+    if (n == 0) return VOR_OK;
+    const int T = 256;
+    k_vertex_quotients<<<(unsigned)((n + T - 1) / T), T, 0, (cudaStream_t)stream>>>(
+        (const long long *)d_num, (const unsigned long long *)d_den, (long long)n, d_out);
+    g_launches++;
+    return cudaGetLastError() == cudaSuccess ? VOR_OK : VOR_E_CUDA;
+}
 
 int32_t vor_autotune_grid(vor_opts *cand, int32_t max) {
     // lanes per cell (1: one thread per cell and the two persistent passes;

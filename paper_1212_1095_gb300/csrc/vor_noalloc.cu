@@ -12,10 +12,12 @@
 // The array's name in host code is only a host-side stand-in for the device
 // symbol, not a device address: a kernel handed it would fault or, where the
 // GPU can reach host memory, silently use the wrong memory.  The device
-// address is therefore looked up with cudaGetSymbolAddress, once per device,
-// with that device current, and cached.
+// address is therefore looked up with cudaGetSymbolAddress on every call,
+// with the caller's device current.  The address is not cached: it belongs
+// to the context that is current at the call, and after cudaDeviceReset (or
+// under another context on the same device) the module is loaded again at
+// another address.  The lookup allocates nothing.
 #include <cstring>
-#include <mutex>
 
 #include <cuda_runtime.h>
 
@@ -25,25 +27,15 @@
 namespace {
 
 constexpr size_t kScratchBytes = VOR_NOALLOC_SCRATCH_BYTES;
-constexpr int kMaxDevices = 64;
 
 __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-std::mutex g_mu;
-void *g_scratch_addr[kMaxDevices] = {};
-
-// Device address of g_scratch on the current device (looked up on the first
-// call for that device).  Returns nullptr on failure.
+// Device address of g_scratch in the context current on the calling thread.
+// Returns nullptr on failure.
 void *scratch_address() {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return nullptr;
-        g_scratch_addr[dev] = p;
-    }
-    return g_scratch_addr[dev];
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return nullptr;
+    return p;
 }
 
 }  // namespace

@@ -102,3 +102,21 @@ def test_kernel_fingerprint_does_not_depend_on_the_checkout_path(monkeypatch):
     assert _build.kernel_fingerprint(names) == h
     monkeypatch.setattr(_build, "FLAGS", moved + ["-DSOMETHING_ELSE"])
     assert _build.kernel_fingerprint(names) != h
+
+
+def test_noalloc_size_limit_matches_its_documentation(lib):
+    # the largest n whose workspace fits the static scratch of
+    # vor_build_noalloc (2^20 box, default options) is the number vor.h states
+    text = open(os.path.join(HEADER, "vor.h")).read()
+    scratch = int(re.search(r"VOR_NOALLOC_SCRATCH_BYTES \(\(size_t\)(\d+) << 20\)", text).group(1)) << 20
+    stated = int(re.search(r"up to ([\d,]+) sites in a 2\^20", text).group(1).replace(",", ""))
+    o = vg.vor_opts_default()
+    lo, hi = 1, 1 << 22
+    while hi - lo > 1:                         # workspace bytes grow with n
+        mid = (lo + hi) // 2
+        if vg.vor_workspace_bytes(mid, 1 << 20, o) <= scratch:
+            lo = mid
+        else:
+            hi = mid
+    assert vg.vor_workspace_bytes(lo, 1 << 20, o) <= scratch < vg.vor_workspace_bytes(lo + 1, 1 << 20, o)
+    assert lo == stated

@@ -296,6 +296,20 @@ def test_plain_equals_bucketed_at_scale():
     assert a["stats"][:, 3].sum() / a["stats"][:, 0].sum() < 500
 
 
+@pytest.mark.parametrize("beta,side", [(1, None), (1, 2000), (2, 50000), (4, None)])
+def test_bucketed_output_is_independent_of_beta_and_side(beta, side):
+    # Method A.6 takes any bucket side s > 0 and any integer beta > 0;
+    # Proposition A.8: the endpoint is the exact first hit for every such
+    # choice, so every choice returns the plain method's cells.  (The stored
+    # digests of the large clustered workloads use beta = 1.)
+    box = 1 << 20
+    xy = synth.gaussian_mixture_sites(3000, seed=77, sigma=3000.0)
+    ref = oracle.cells(xy, box, "plain")
+    got = oracle.cells(xy, box, "bucketed", beta=beta, bucket_side=side)
+    for key in ("cell_ptr", "labels", "vnum", "delaunay"):
+        assert np.array_equal(got[key], ref[key]), key
+
+
 # ---------------------------------------------------- Method A.6 worked example
 
 def test_si_worked_example():

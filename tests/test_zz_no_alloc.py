@@ -44,19 +44,23 @@ def _outputs(n, dev):
     return bufs, out
 
 
-def _noalloc(xy):
-    """One call of vor_build_noalloc through the C ABI; returns host arrays."""
+def _call(sites, n, out):
     lib = vg.library()
-    dev = torch.device("cuda", torch.cuda.current_device())
-    sites = torch.from_numpy(np.ascontiguousarray(xy, dtype=np.int32)).to(dev)
-    n = xy.shape[0]
-    bufs, out = _outputs(n, dev)
     opts = vg.vor_opts_default()
     stream = torch.cuda.current_stream()
     rc = lib.vor_build_noalloc(ctypes.c_void_p(sites.data_ptr()), n, vg.VorBox(BOX, BOX),
                                ctypes.byref(opts), ctypes.byref(out),
                                ctypes.c_void_p(stream.cuda_stream))
     assert rc == 0, vg.vor_strerror(rc)
+
+
+def _noalloc(xy):
+    """One call of vor_build_noalloc through the C ABI; returns host arrays."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    sites = torch.from_numpy(np.ascontiguousarray(xy, dtype=np.int32)).to(dev)
+    n = xy.shape[0]
+    bufs, out = _outputs(n, dev)
+    _call(sites, n, out)
     ne, nd = (int(v) for v in bufs["totals"].cpu())
     return {"cell_ptr": bufs["cell_ptr"].cpu().numpy(), "labels": bufs["labels"][:ne].cpu().numpy(),
             "vx": bufs["vx"][:ne].cpu().numpy(), "vy": bufs["vy"][:ne].cpu().numpy(),
@@ -94,3 +98,19 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     rc = lib.vor_build_noalloc(ctypes.c_void_p(0), n, vg.VorBox(BOX, BOX), ctypes.byref(opts),
                                ctypes.byref(out), ctypes.c_void_p(0))
     assert rc == -9
+
+
+def test_noalloc_allocates_no_device_memory():
+    # inputs and outputs allocated up front; after one warm-up call (which
+    # may load the library's scratch array), a second call leaves the free
+    # device memory exactly where it was
+    dev = torch.device("cuda", torch.cuda.current_device())
+    xy = synth.uniform_sites(50000, seed=33)
+    sites = torch.from_numpy(xy).to(dev)
+    bufs, out = _outputs(xy.shape[0], dev)
+    _call(sites, xy.shape[0], out)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    _call(sites, xy.shape[0], out)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
