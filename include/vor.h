@@ -54,7 +54,7 @@ extern "C" {
 #define VOR_E_DUPLICATE (-3)     /* two equal sites                          */
 #define VOR_E_BOX_TOO_LARGE (-4) /* w or h outside [2, 2^20]                 */
 #define VOR_E_OOM (-5)           /* workspace or output too small / no memory */
-#define VOR_E_CAPACITY (-6)      /* a cell exceeded the large-cell capacities */
+#define VOR_E_CAPACITY (-6)      /* a capacity of the build was exceeded     */
 #define VOR_E_CUDA (-7)          /* a CUDA runtime call failed               */
 #define VOR_E_INTERNAL (-8)      /* an internal consistency check failed     */
 #define VOR_E_SCRATCH_LIMIT (-9) /* vor_build_noalloc: n needs more than its static scratch */
@@ -100,8 +100,8 @@ typedef struct vor_stats {
     uint64_t rays_first_pass;  /* the part of rays shot by the first thread-per-cell pass  */
     uint64_t evals_second_pass;/* the part of evals done by the second thread-per-cell pass*/
     uint64_t medium_cells;     /* cells handed to the warp-per-cell medium tier            */
-    uint64_t large_cells;      /* cells handed on to the warp-per-cell large tier          */
-    uint64_t reserved[1];
+    uint64_t large_cells;      /* cells handed on to the block-per-cell tier               */
+    uint64_t global_cells;     /* of those, cells too large for its shared-memory mode     */
 } vor_stats;
 
 /* Device output buffers, allocated by the caller with the capacities below:
@@ -206,7 +206,7 @@ int vor_stage_ms(float *ms, int max_stages);
  * device array of VOR_NOALLOC_SCRATCH_BYTES (64 MiB) inside the library; it
  * occupies that memory on every GPU where it has been loaded until the
  * process exits.  n must satisfy vor_workspace_bytes(n, box, opts) <=
- * VOR_NOALLOC_SCRATCH_BYTES (up to 101,656 sites in a 2^20 x 2^20 box with the
+ * VOR_NOALLOC_SCRATCH_BYTES (up to 85,664 sites in a 2^20 x 2^20 box with the
  * default options); larger n is rejected with VOR_E_SCRATCH_LIMIT before any
  * work is launched.  No cudaMalloc, cudaFree or other allocating routine is called.
  *

@@ -71,7 +71,7 @@ class VorStats(ctypes.Structure):
                 ("max_edges", ctypes.c_uint64), ("widenings", ctypes.c_uint64),
                 ("evals_first_pass", ctypes.c_uint64), ("rays_first_pass", ctypes.c_uint64),
                 ("evals_second_pass", ctypes.c_uint64), ("medium_cells", ctypes.c_uint64),
-                ("large_cells", ctypes.c_uint64), ("reserved", ctypes.c_uint64 * 1)]
+                ("large_cells", ctypes.c_uint64), ("global_cells", ctypes.c_uint64)]
 
     def as_dict(self) -> dict:
         return {f: int(getattr(self, f)) for f, _ in self._fields_ if f != "reserved"}

@@ -19,7 +19,8 @@ BUILD = os.path.join(HERE, "_build")
 SO = os.path.join(BUILD, "libvor.so")
 
 SOURCES = ["vor_lib.cu", "vor_cells.cu", "vor_cells_t1.cu", "vor_cells_g2_4.cu",
-           "vor_cells_g8_16.cu", "vor_cells_g32.cu", "vor_noalloc.cu", "vor_server.cu"]
+           "vor_cells_g8_16.cu", "vor_cells_g32.cu", "vor_cells_coop.cu", "vor_noalloc.cu",
+           "vor_server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE,
          "-I" + CSRC]

@@ -1,11 +1,10 @@
 // vor_cells.cu -- launchers of the projector kernel: lane-count dispatch of
-// the first pass and the large-cell pass (one warp per deferred cell).
+// the multi-lane first pass and the medium tier (one warp per deferred cell).
 #include "vor_cells.cuh"
 
 namespace vor {
 
 int cells_fast_max_smem() { return (int)(F_GROUPS * sizeof(FastSmem)); }
-int cells_large_capacity() { return L_CMAX; }
 
 cudaError_t launch_cells_fast(const CellParams &P, int lanes, cudaStream_t st) {
     switch (lanes) {
@@ -30,9 +29,8 @@ static cudaError_t launch_tier(const CellParams &P, int max_cells, cudaStream_t 
     return cudaGetLastError();
 }
 
-cudaError_t launch_cells_large(const CellParams &P, int tier, int max_cells, cudaStream_t st) {
-    if (tier == 0) return launch_tier<M_CMAX, M_SMAX, M_EMAX, M_RMAX>(P, max_cells, st);
-    return launch_tier<L_CMAX, L_SMAX, L_EMAX, L_RMAX>(P, max_cells, st);
+cudaError_t launch_cells_medium(const CellParams &P, int max_cells, cudaStream_t st) {
+    return launch_tier<M_CMAX, M_SMAX, M_EMAX, M_RMAX>(P, max_cells, st);
 }
 
 }  // namespace vor

@@ -983,15 +983,13 @@ cells_kernel(CellParams P) {
 // ---- configurations ----------------------------------------------------------
 // first pass: 16 groups per block, small capacities, bounded certificate work
 constexpr int F_CMAX = 48, F_SMAX = 20, F_EMAX = 40, F_RMAX = 40, F_GROUPS = 16;
-// large-cell passes: one warp per cell, one cell per block; the medium tier
-// (about 7 KB of shared memory per warp) takes the deferred cells first and
-// hands the ones that exceed it to the large tier
+// the medium tier: one warp per cell, one cell per block (about 7 KB of
+// shared memory per warp); it hands the cells that exceed it to the
+// block-per-cell tier (vor_cells_coop.cuh)
 constexpr int M_CMAX = 256, M_SMAX = 64, M_EMAX = 64, M_RMAX = 256;
-constexpr int L_CMAX = 1024, L_SMAX = 256, L_EMAX = 256, L_RMAX = 1024;
 
 using FastSmem = GroupSmem<F_CMAX, F_SMAX, F_EMAX>;
 using MediumSmem = GroupSmem<M_CMAX, M_SMAX, M_EMAX>;
-using LargeSmem = GroupSmem<L_CMAX, L_SMAX, L_EMAX>;
 
 template <int G>
 cudaError_t launch_fast_g(const CellParams &P, cudaStream_t st) {

@@ -34,10 +34,12 @@ struct WsHeader {
     unsigned long long stats[STAT_N];
     int large_next;         // next cell of the medium-cell pass (dynamic schedule)
     int m_total;            // buckets over all sets (set by the grid choice)
-    int ndeferred3;         // cells handed from the medium to the large tier
-    int large_next2;        // next cell of the large tier
+    int ndeferred3;         // cells handed from the medium tier to the block-per-cell tier
+    int coop_next;          // next cell of the block-per-cell tier (shared-memory mode)
     int pass_next[2];       // next list entry of the two thread-per-cell passes
-    long long pad[9];
+    int ndeferred4;         // cells handed on to the global-memory mode of that tier
+    int coop_next2;         // next cell of the global-memory mode
+    long long pad[8];
 };
 static_assert(sizeof(WsHeader) <= 256, "header");
 
@@ -164,10 +166,15 @@ cudaError_t launch_cells_pass(const CellParams &P, int pass, int *gcount, long l
                               float2 *gtab, int *glab, cudaStream_t st);
 int pass_gather_width();
 long long gather_rows(long long n);   // list rows: n rounded up to whole tiles of 32
-// one warp per cell over P.cell_list, cells taken from *P.next_cell; tier 0:
-// medium capacities (defers to P.deferred), tier 1: large capacities
-cudaError_t launch_cells_large(const CellParams &P, int tier, int max_cells, cudaStream_t st);
+// one warp per cell over P.cell_list, cells taken from *P.next_cell, with
+// the medium capacities (defers to P.deferred)
+cudaError_t launch_cells_medium(const CellParams &P, int max_cells, cudaStream_t st);
 int cells_fast_max_smem();
-int cells_large_capacity();
+// one block per cell over P.cell_list (vor_cells_coop.cu): shared-memory
+// mode (defers to P.deferred) or global-memory mode (slices of the arena,
+// each for sets of at most nmax sites)
+cudaError_t launch_cells_coop(const CellParams &P, bool global_mode, char *arena, int slices,
+                              long long nmax, int max_cells, cudaStream_t st);
+long long coop_slice_bytes(long long nmax);
 
 }  // namespace vor

@@ -712,10 +712,25 @@ struct Layout {
     int s_fixed, lanes, target, n_sets, load_pct;
     long long n, m_sum, g_sum;
     size_t hdr, sets, sset, bstart, rank, sxy, sid, partial, ecount, dcount, loc, del_ptr, slot,
-        spill, deferred, deferred2, deferred3, gcount, grho2, gtab, glab, coarse, total;
+        spill, deferred, deferred2, deferred3, deferred4, gcount, grho2, gtab, glab, coarse, coop,
+        total;
     int spill_cap;
     int n_partial;
+    long long n_max;          // largest set
+    int coop_slices;          // global-memory slices of the block-per-cell tier
 };
+
+// Slices of the block-per-cell tier's global-memory mode: one slice holds a
+// cell of the largest set whatever its size; a batch of many sets gets up to
+// 64 slices within 16 bytes per site.
+constexpr int COOP_MAX_SLICES = 64;
+static int coop_slices_for(long long n_total, long long n_max) {
+    const long long slice = coop_slice_bytes(n_max);
+    long long k = slice > 0 ? 16 * n_total / slice : 1;
+    if (k < 1) k = 1;
+    if (k > COOP_MAX_SLICES) k = COOP_MAX_SLICES;
+    return (int)k;
+}
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -736,6 +751,7 @@ static bool resolve(const int64_t *set_ptr, const vor_box *boxes, int n_sets, in
     L.n_sets = n_sets;
     L.m_sum = 0;
     L.g_sum = 0;
+    L.n_max = 1;
     if (set_ptr && set_ptr[0] != 0) return false;
     for (int j = 0; j < n_sets; j++) {
         const int64_t a = set_ptr ? set_ptr[j] : 0, b = set_ptr ? set_ptr[j + 1] : n1;
@@ -746,6 +762,7 @@ static bool resolve(const int64_t *set_ptr, const vor_box *boxes, int n_sets, in
         if (!plan_set(b - a > 0 ? b - a : 1, bx.w, bx.h, L.s_fixed, pl)) return false;
         L.m_sum += pl.m_max;
         L.g_sum += (long long)pl.G * pl.G;
+        if (b - a > L.n_max) L.n_max = b - a;
     }
     L.n = set_ptr ? set_ptr[n_sets] : n1;
     if (L.n < 0 || L.n > (1 << 27) || L.m_sum > (1ll << 30)) return false;
@@ -778,11 +795,14 @@ static bool resolve(const int64_t *set_ptr, const vor_box *boxes, int n_sets, in
     L.deferred = at; at = align256(at + nn * 4);
     L.deferred2 = at; at = align256(at + nn * 4);
     L.deferred3 = at; at = align256(at + nn * 4);
+    L.deferred4 = at; at = align256(at + nn * 4);
     L.gcount = at;   at = align256(at + nn * 4);
     L.grho2 = at;    at = align256(at + nn * 8);
     L.gtab = at;     at = align256(at + (size_t)gather_rows(nn) * 8 * (size_t)pass_gather_width());
     L.glab = at;     at = align256(at + (size_t)gather_rows(nn) * 4 * (size_t)pass_gather_width());
     L.coarse = at;   at = align256(at + (size_t)L.g_sum * 4);
+    L.coop_slices = coop_slices_for((long long)nn, L.n_max);
+    L.coop = at;     at = align256(at + (size_t)L.coop_slices * (size_t)coop_slice_bytes(L.n_max));
     L.total = at;
     return true;
 }
@@ -834,6 +854,7 @@ static int launch_build(const BatchArgs &A, const vor_opts *o, void *ws, const L
     int *deferred = (int *)(base + L.deferred);
     int *deferred2 = (int *)(base + L.deferred2);
     int *deferred3 = (int *)(base + L.deferred3);
+    int *deferred4 = (int *)(base + L.deferred4);
     int *coarse = (int *)(base + L.coarse);
     const int2 *sites = A.sites;
 
@@ -933,7 +954,9 @@ static int launch_build(const BatchArgs &A, const vor_opts *o, void *ws, const L
         mark(3, st);
         mark(4, st);
     }
-    // warp per cell for what is left: medium capacities, then large
+    // what is left: one warp per cell (medium capacities), then one block per
+    // cell with its arrays in shared memory, then in global memory (room for
+    // every site of the set: no valid cell is refused)
     CellParams PM = P;
     PM.need_out = nullptr;
     PM.need_in = nullptr;
@@ -943,15 +966,25 @@ static int launch_build(const BatchArgs &A, const vor_opts *o, void *ws, const L
     PM.deferred = deferred3;
     PM.deferred_count = &hdr->ndeferred3;
     PM.next_cell = &hdr->large_next;
-    if (launch_cells_large(PM, 0, n, st) != cudaSuccess) return VOR_E_CUDA;
+    if (launch_cells_medium(PM, n, st) != cudaSuccess) return VOR_E_CUDA;
     CellParams PL = PM;
     PL.cell_list = deferred3;
     PL.list_count = &hdr->ndeferred3;
-    PL.deferred = nullptr;
-    PL.deferred_count = nullptr;
-    PL.next_cell = &hdr->large_next2;
-    if (launch_cells_large(PL, 1, n, st) != cudaSuccess) return VOR_E_CUDA;
-    launched += 2;
+    PL.deferred = deferred4;
+    PL.deferred_count = &hdr->ndeferred4;
+    PL.next_cell = &hdr->coop_next;
+    char *arena = base + L.coop;
+    if (launch_cells_coop(PL, false, arena, L.coop_slices, L.n_max, n, st) != cudaSuccess)
+        return VOR_E_CUDA;
+    CellParams PG = PL;
+    PG.cell_list = deferred4;
+    PG.list_count = &hdr->ndeferred4;
+    PG.deferred = nullptr;
+    PG.deferred_count = nullptr;
+    PG.next_cell = &hdr->coop_next2;
+    if (launch_cells_coop(PG, true, arena, L.coop_slices, L.n_max, n, st) != cudaSuccess)
+        return VOR_E_CUDA;
+    launched += 3;
     mark(5, st);
 
     launched += scan<long long>(ecount, n, nullptr, (long long *)out->cell_ptr, partial,
@@ -1121,6 +1154,7 @@ int vor_status(const void *d_workspace, void *stream, vor_stats *stats) {
         stats->evals_second_pass = h.stats[STAT_EVALS2];
         stats->medium_cells = (uint64_t)(h.ndeferred2 > 0 ? h.ndeferred2 : 0);
         stats->large_cells = (uint64_t)(h.ndeferred3 > 0 ? h.ndeferred3 : 0);
+        stats->global_cells = (uint64_t)(h.ndeferred4 > 0 ? h.ndeferred4 : 0);
     }
     return map_err(h.err);
 }
@@ -1338,7 +1372,7 @@ const char *vor_strerror(int code) {
     case VOR_E_DUPLICATE: return "two sites are equal";
     case VOR_E_BOX_TOO_LARGE: return "box side outside [2, 2^20]";
     case VOR_E_OOM: return "workspace or output buffer too small, or out of memory";
-    case VOR_E_CAPACITY: return "a cell exceeded the large-cell capacity";
+    case VOR_E_CAPACITY: return "a cell exceeded a capacity of the build";
     case VOR_E_CUDA: return "CUDA runtime error";
     case VOR_E_INTERNAL: return "internal consistency check failed";
     case VOR_E_SCRATCH_LIMIT: return "n needs more workspace than the static scratch of vor_build_noalloc";

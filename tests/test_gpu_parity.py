@@ -134,3 +134,38 @@ def test_host_entry_point_matches_device_entry_point():
     b = to_numpy(vg.build_host(xy, BOX))
     for key in ("cell_ptr", "labels", "vx", "vy", "delaunay"):
         assert np.array_equal(a[key], b[key]), key
+
+
+def _hub_rows(cx, cy, d, m):
+    """m sites on four rows around the hub (cx, cy), each row at distance d
+    from it and its sites within 0.4 d of the row's foot: the bisectors of
+    the hub with the sites of a row all touch one parabola (focus the hub),
+    so every site of every row carries an edge of the hub's cell, which has
+    exactly m edges."""
+    k = m // 4
+    step = max(1, int(0.8 * d) // k)
+    t = np.round((np.arange(k) - (k - 1) / 2.0) * step).astype(np.int64)
+    rows = [np.stack([t, np.full(k, -d)], 1), np.stack([np.full(k, d), t], 1),
+            np.stack([-t, np.full(k, d)], 1), np.stack([np.full(k, -d), -t], 1)]
+    return np.concatenate(rows) + np.array([cx, cy])
+
+
+@pytest.mark.parametrize("m", [1000, 5000])
+def test_hub_cells_with_thousands_of_edges(m):
+    # one cell with m edges: beyond the shared-memory capacities of the
+    # block-per-cell tier for m = 5000 (its global-memory mode), within them
+    # for m = 1000; the oracle has no size limit and neither has the library
+    u = synth.uniform_sites(3000, seed=m)
+    u = u[np.maximum(np.abs(u[:, 0] - 500000), np.abs(u[:, 1] - 500000)) > 25000]
+    xy = np.concatenate([[[500000, 500000]], _hub_rows(500000, 500000, 10000, m), u]).astype(np.int32)
+    r = oracle.cells(xy, BOX, "bucketed", beta=1)
+    assert np.diff(r["cell_ptr"])[0] == m
+    d = gpu(xy, BOX, collect_stats=1)
+    assert_full_parity(d, r)
+    # and inside a batch, next to an ordinary set
+    u = synth.uniform_sites(2000, seed=7)
+    ptr = np.array([0, xy.shape[0], xy.shape[0] + u.shape[0]], np.int64)
+    B = vg.build_batch(torch.from_numpy(np.concatenate([xy, u])).cuda(), ptr,
+                       np.full((2, 2), BOX, np.int32))
+    assert_full_parity(to_numpy(B.set(0)), r)
+    assert_full_parity(to_numpy(B.set(1)), oracle.cells(u, BOX, "plain"))

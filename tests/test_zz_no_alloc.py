@@ -83,7 +83,7 @@ def _same(a, b):
 
 def test_noalloc_matches_regular_entry_point_on_two_calls():
     # the second call reuses the scratch the first call left behind
-    first = synth.uniform_sites(90000, seed=31)
+    first = synth.uniform_sites(80000, seed=31)
     second = synth.gaussian_mixture_sites(40000, seed=32, sigma=3000.0)
     for xy in (first, second):
         _same(_noalloc(xy), _regular(xy))
