@@ -99,6 +99,7 @@ typedef struct vor_stats {
     uint64_t evals_first_pass; /* the part of evals done by the first thread-per-cell pass */
     uint64_t rays_first_pass;  /* the part of rays shot by the first thread-per-cell pass  */
     uint64_t evals_second_pass;/* the part of evals done by the second thread-per-cell pass*/
+    uint64_t third_pass_cells; /* cells handed to the third thread-per-cell pass           */
     uint64_t medium_cells;     /* cells handed to the warp-per-cell medium tier            */
     uint64_t large_cells;      /* cells handed on to the block-per-cell tier               */
     uint64_t global_cells;     /* of those, cells too large for its shared-memory mode     */
@@ -206,7 +207,7 @@ int vor_stage_ms(float *ms, int max_stages);
  * device array of VOR_NOALLOC_SCRATCH_BYTES (64 MiB) inside the library; it
  * occupies that memory on every GPU where it has been loaded until the
  * process exits.  n must satisfy vor_workspace_bytes(n, box, opts) <=
- * VOR_NOALLOC_SCRATCH_BYTES (up to 85,664 sites in a 2^20 x 2^20 box with the
+ * VOR_NOALLOC_SCRATCH_BYTES (up to 85,228 sites in a 2^20 x 2^20 box with the
  * default options); larger n is rejected with VOR_E_SCRATCH_LIMIT before any
  * work is launched.  No cudaMalloc, cudaFree or other allocating routine is called.
  *

@@ -70,7 +70,8 @@ class VorStats(ctypes.Structure):
                 ("deferred", ctypes.c_uint64), ("candidates", ctypes.c_uint64),
                 ("max_edges", ctypes.c_uint64), ("widenings", ctypes.c_uint64),
                 ("evals_first_pass", ctypes.c_uint64), ("rays_first_pass", ctypes.c_uint64),
-                ("evals_second_pass", ctypes.c_uint64), ("medium_cells", ctypes.c_uint64),
+                ("evals_second_pass", ctypes.c_uint64), ("third_pass_cells", ctypes.c_uint64),
+                ("medium_cells", ctypes.c_uint64),
                 ("large_cells", ctypes.c_uint64), ("global_cells", ctypes.c_uint64)]
 
     def as_dict(self) -> dict:

@@ -62,7 +62,6 @@ struct CoopView {
 
 struct CoopCtl {
     int ncand, flag, ne, qhead, qtail, qtake, err;
-    int hist[32];
     Hit init[3];
     float red[CO_NW];
     int ired[CO_NW];
@@ -346,22 +345,23 @@ __device__ float coop_vertices(const CoopView &V, CoopCtl &K, int e) {
     return block_max(R2, K);
 }
 
-// scan_rows of vor_cells.cuh for one warp of the block: the warp reads the
-// bucket rows by0 + 32 w + lane, by0 + 32 (w + NW) + lane, ...
-template <int NSPAN, int ILP, class RowSpans, class Visit>
-__device__ __forceinline__ void coop_scan_rows(const CellGrid &g, const int2 *__restrict__ sxy, int by0,
-                                               int by1, RowSpans row_spans, Visit visit) {
+// scan_rows of vor_cells.cuh spread over the block: the rows are
+// row_of(k) for k in [kb, ke), warp w taking k = kb + 32 w + lane,
+// kb + 32 (w + NW) + lane, ...; row_of returns -1 for no row
+template <int NSPAN, int ILP, class RowOf, class RowSpans, class Visit>
+__device__ __forceinline__ void coop_scan_rows(const CellGrid &g, const int2 *__restrict__ sxy, int kb,
+                                               int ke, RowOf row_of, RowSpans row_spans, Visit visit) {
     const unsigned FULL = 0xffffffffu;
     const int w = threadIdx.x >> 5, gl = threadIdx.x & 31;
-    for (int r0 = by0 + 32 * w; r0 <= by1; r0 += 32 * CO_NW) {
-        const int row = r0 + gl;
+    for (int r0 = kb + 32 * w; r0 < ke; r0 += 32 * CO_NW) {
+        const int row = r0 + gl < ke ? row_of(r0 + gl) : -1;
         int x0[NSPAN], x1[NSPAN];
         int ns = 0;
-        if (row <= by1) ns = row_spans(row, x0, x1);
+        if (row >= 0) ns = row_spans(row, x0, x1);
         int nmax = ns;
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) nmax = max(nmax, __shfl_xor_sync(FULL, nmax, off));
-        const int *rb = g.bs + (size_t)(row <= by1 ? row : by0) * g.m1;
+        const int *rb = g.bs + (size_t)(row >= 0 ? row : 0) * g.m1;
 #pragma unroll
         for (int k = 0; k < NSPAN; k++) {
             if (k >= nmax) break;
@@ -401,29 +401,19 @@ __device__ __forceinline__ void coop_scan_rows(const CellGrid &g, const int2 *__
     }
 }
 
-// Append the sites with r2lo < |a - p|^2 <= r2hi (all, or with cut_only
-// those cutting the polygon of e vertices, reading only the flower's parts
-// of the rows) to the candidates; K.flag = 1 when the table would overflow.
+// Append every site a != p with |a - p|^2 <= r2 to the candidates (the
+// first disc); K.flag = 1 when the table would overflow.
 __device__ void coop_scan_disc(const CellParams &P, const CellGrid &g, const CoopView &V, CoopCtl &K,
-                               const int2 p, const int self, const i64 r2lo, const i64 r2hi,
-                               const bool cut_only, const int e, Counters &cnt) {
+                               const int2 p, const int self, const i64 r2, Counters &cnt) {
     const int s = g.s;
-    const int r = (int)ceilf(sqrtf((float)r2hi)) + 1;
+    const int r = (int)ceilf(sqrtf((float)r2)) + 1;
     const int by0 = p.y - r <= 0 ? 0 : (p.y - r) / s;
     const int by1 = min(g.m2 - 1, (p.y + r) / s);
-    const float binscale = 32.f / (float)max(r2hi - r2lo, (i64)1);
     const int cap = V.cap;
     auto visit = [&](int pos, int2 q) {
         if (pos == self) return;
         const int nx = q.x - p.x, ny = q.y - p.y;
-        const i64 cc = (i64)nx * nx + (i64)ny * ny;
-        if (cc <= r2lo || cc > r2hi) return;
-        if (cut_only) {
-            cnt.annulus++;
-            if (!cuts_polygon(V, e, nx, ny, cc)) return;
-            const int bin = min(31, max(0, (int)((float)(cc - r2lo) * binscale)));
-            atomicAdd(&K.hist[bin], 1);
-        }
+        if ((i64)nx * nx + (i64)ny * ny > r2) return;
         const int at = atomicAdd(&K.ncand, 1);
         if (at < cap) {
             const float fnx = (float)nx, fny = (float)ny, rc = 1.f / fmaf(fnx, fnx, fny * fny);
@@ -433,17 +423,72 @@ __device__ void coop_scan_disc(const CellParams &P, const CellGrid &g, const Coo
             K.flag = 1;
         }
     };
-    if (cut_only) {
-        auto spans = [&](int row, int *x0, int *x1) -> int {
-            return flower_row_spans(g, V, e, p, r2lo, r2hi, row, x0, x1);
-        };
-        coop_scan_rows<5, 2>(g, P.sxy, by0, by1, spans, visit);
-    } else {
-        auto span = [&](int row, int *x0, int *x1) -> int {
-            return disc_row_span(g, row, p.x, p.y, r2hi, x0[0], x1[0]) && x0[0] <= x1[0] ? 1 : 0;
-        };
-        coop_scan_rows<1, 2>(g, P.sxy, by0, by1, span, visit);
+    auto row_of = [&](int k) { return by0 + k; };
+    auto span = [&](int row, int *x0, int *x1) -> int {
+        return disc_row_span(g, row, p.x, p.y, r2, x0[0], x1[0]) && x0[0] <= x1[0] ? 1 : 0;
+    };
+    coop_scan_rows<1, 2>(g, P.sxy, 0, by1 - by0 + 1, row_of, span, visit);
+}
+
+// The bucket rows in order of distance from p's row: k = 0, 1, 2, 3, ... is
+// row prow, prow + 1, prow - 1, prow + 2, ...
+__device__ __forceinline__ int sweep_row(const CellGrid &g, int prow, int k) {
+    const int h = (k + 1) >> 1;
+    const int row = (k & 1) ? prow + h : prow - h;
+    return row >= 0 && row < g.m2 ? row : -1;
+}
+
+// One step of the certificate sweep: the rows sweep_row(k) for k in
+// [k0, k0 + len).  The sites with r2lo < |a - p|^2 <= r2hi that cut the
+// polygon of e vertices (reading only the parts of each row that meet a
+// vertex disc) are appended to the candidates; once the table is full
+// (K.flag) the step adds nothing more and is repeated, over fewer rows,
+// after the next projector run.
+__device__ void coop_sweep_step(const CellParams &P, const CellGrid &g, const CoopView &V, CoopCtl &K,
+                                const int2 p, const int self, const i64 r2lo, const i64 r2hi,
+                                const int e, const int prow, const int k0, const int len,
+                                Counters &cnt) {
+    const int cap = V.cap;
+    auto visit = [&](int pos, int2 q) {
+        if (pos == self) return;
+        const int nx = q.x - p.x, ny = q.y - p.y;
+        const i64 cc = (i64)nx * nx + (i64)ny * ny;
+        if (cc <= r2lo || cc > r2hi) return;
+        cnt.annulus++;
+        if (K.flag || !cuts_polygon(V, e, nx, ny, cc)) return;
+        const int at = atomicAdd(&K.ncand, 1);
+        if (at < cap) {
+            const float fnx = (float)nx, fny = (float)ny, rc = 1.f / fmaf(fnx, fnx, fny * fny);
+            V.cand[at] = make_float4(fnx, fny, rc, (float)(abs(nx) + abs(ny)) * rc);
+            V.lab[at] = P.sid[pos] - g.site_base;
+        } else {
+            K.flag = 1;
+        }
+    };
+    auto row_of = [&](int k) { return sweep_row(g, prow, k); };
+    auto spans = [&](int row, int *x0, int *x1) -> int {
+        return flower_row_spans(g, V, e, p, r2lo, r2hi, row, x0, x1);
+    };
+    coop_scan_rows<5, 2>(g, P.sxy, k0, k0 + len, row_of, spans, visit);
+}
+
+// Keep only the candidates whose lines carry an edge of the polygon (edge q
+// becomes candidate q; the other half-planes contain this polygon and every
+// later one), through the queue as scratch.
+__device__ void coop_prune(const CoopView &V, int e) {
+    float4 *tc = reinterpret_cast<float4 *>(V.q);
+    int *tl = reinterpret_cast<int *>(tc + e);
+    for (int q = threadIdx.x; q < e; q += CO_T) {
+        tc[q] = V.cand[V.emit[q]];
+        tl[q] = V.lab[V.emit[q]];
     }
+    __syncthreads();
+    for (int q = threadIdx.x; q < e; q += CO_T) {
+        V.cand[q] = tc[q];
+        V.lab[q] = tl[q];
+        V.emit[q] = q;
+    }
+    __syncthreads();
 }
 
 // One cell with the whole block.  Returns CELL_OK (output written),
@@ -474,7 +519,7 @@ __device__ int coop_cell(const CellParams &P, const CoopView &V, CoopCtl &K, int
     for (int attempt = 0;; attempt++) {
         if (tid == 0) { K.ncand = 0; K.flag = 0; }
         __syncthreads();
-        coop_scan_disc(P, g, V, K, p, i, -1, rho2, false, 0, cnt);
+        coop_scan_disc(P, g, V, K, p, i, rho2, cnt);
         __syncthreads();
         if (!K.flag) break;
         if (attempt >= 24 || rho2 <= 4) return CELL_DEFER;
@@ -503,60 +548,71 @@ __device__ int coop_cell(const CellParams &P, const CoopView &V, CoopCtl &K, int
     if (rc != CO_OK) return rc == CO_CAP ? CELL_DEFER : CELL_FAIL;
     int e = K.ne;
 
-    // ---- 3. vertex-disc certificate (see certify_by_vertex_discs) --------------
+    // ---- 3. vertex-disc certificate, outward sweeps of bucket rows -----------
+    // Invariant: every site within rho of p is a candidate or cuts no polygon
+    // from here on (polygons only shrink, and so do their vertex discs).  A
+    // round stops when 2R <= rho (Lemmas Byy'Syy' and SitesInLargeSquare) or
+    // rho covers the box; else it sweeps the rows outward from p's row over
+    // the annulus rho < |a - p| <= min(2R, 2 rho), adding the sites that cut
+    // the current polygon, and reruns the projector whenever cutters
+    // accumulate (or the table fills: the step is then repeated over fewer
+    // rows), which shrinks the polygon, its vertex discs and the annulus
+    // still to sweep.  After the sweep every site within the annulus's final
+    // outer radius has been seen: rho grows to it.
+    const int prow = p.y / s;
     for (int round = 0;; round++) {
         if (tid == 0) K.flag = 0;
         __syncthreads();
-        const float R2 = coop_vertices(V, K, e);
+        float R2 = coop_vertices(V, K, e);
         if (K.flag == 2) return CELL_FAIL;
-        const i64 need = (i64)(4.f * (R2 * (1.f + 0x1p-12f) + 1.f)) + 1;   // > (2R)^2
+        i64 need = (i64)(4.f * (R2 * (1.f + 0x1p-12f) + 1.f)) + 1;   // > (2R)^2
         if (need <= rho2 || rho2 >= far2) break;
-        if (round >= 4096) return CELL_FAIL;
-        // keep the edge lines only (the other half-planes contain every later
-        // polygon): edge q becomes candidate q, through the queue as scratch
-        float4 *tc = reinterpret_cast<float4 *>(V.q);
-        int *tl = reinterpret_cast<int *>(tc + e);
-        for (int q = tid; q < e; q += CO_T) {
-            tc[q] = V.cand[V.emit[q]];
-            tl[q] = V.lab[V.emit[q]];
-        }
-        __syncthreads();
-        for (int q = tid; q < e; q += CO_T) {
-            V.cand[q] = tc[q];
-            V.lab[q] = tl[q];
-            V.emit[q] = q;
-        }
+        if (round >= 64) return CELL_FAIL;
+        coop_prune(V, e);
         C = e;
         if (tid == 0) cnt.widen++;
-        i64 step2 = min(min(need, rho2 < ((i64)1 << 60) / 4 ? 4 * rho2 + 4 : rho2), far2);
-        for (int shrink = 0;; shrink++) {
+        // the next annulus reaches at most twice as far: the nearest cutters
+        // first (they shrink the polygon and its vertex discs the most)
+        i64 r2hi = min(min(need, rho2 < ((i64)1 << 60) / 4 ? 4 * rho2 + 4 : rho2), far2);
+        int ran = C;                                   // candidates the last projector run saw
+        int repeats = 0;
+        int len = CO_T;                                // rows per step: fewer after a full table
+        for (int k0 = 0;;) {
+            const int rmax = (int)(sqrtf((float)r2hi) / (float)s) + 2;   // rows beyond cannot meet
+            const bool last = k0 + len > 2 * rmax + 1;
             if (tid == 0) { K.ncand = C; K.flag = 0; }
-            for (int q = tid; q < 32; q += CO_T) K.hist[q] = 0;
             __syncthreads();
-            coop_scan_disc(P, g, V, K, p, i, rho2, step2, true, e, cnt);
+            coop_sweep_step(P, g, V, K, p, i, rho2, r2hi, e, prow, k0, len, cnt);
             __syncthreads();
-            if (!K.flag) break;
-            if (shrink >= 40 || step2 <= rho2 + 1) return CELL_DEFER;
-            // too many cutters: the annulus up to the last distance bin whose
-            // cutters, with all nearer ones, still fit
-            const int room = V.cap - C;
-            int b = 0, sum = 0;
-            while (b < 32 && sum + K.hist[b] <= room) sum += K.hist[b++];
-            const i64 width = step2 - rho2;
-            step2 = b > 0 ? rho2 + (i64)((double)width * b / 32.0) : rho2 + width / 4;
-            if (step2 <= rho2) step2 = rho2 + 1;
-            __syncthreads();
+            const bool full = K.flag != 0;
+            C = min(K.ncand, V.cap);
+            if (full || C - ran >= 64 || last) {
+                if (C > ran) {
+                    if (tid == 0) { cnt.reruns++; cnt.cands += C - ran; }
+                    rc = coop_projector(V, K, C, P.exact_only, cnt);
+                    if (rc != CO_OK) return rc == CO_CAP ? CELL_DEFER : CELL_FAIL;
+                    e = K.ne;
+                    if (tid == 0) K.flag = 0;
+                    __syncthreads();
+                    R2 = coop_vertices(V, K, e);
+                    if (K.flag == 2) return CELL_FAIL;
+                    need = (i64)(4.f * (R2 * (1.f + 0x1p-12f) + 1.f)) + 1;
+                    r2hi = min(r2hi, need);
+                    coop_prune(V, e);
+                    C = ran = e;
+                }
+                if (full) {                            // the step again, with room, over fewer rows
+                    if (++repeats > 64) return CELL_DEFER;
+                    len = max(len / 2, 8);
+                    continue;
+                }
+            }
+            repeats = 0;
+            if (last) break;
+            k0 += len;
+            len = min(len * 2, CO_T);
         }
-        rho2 = step2;
-        const int ncut = K.ncand - C;
-        __syncthreads();
-        if (ncut > 0) {
-            if (tid == 0) { cnt.reruns++; cnt.cands += ncut; }
-            C += ncut;
-            rc = coop_projector(V, K, C, P.exact_only, cnt);
-            if (rc != CO_OK) return rc == CO_CAP ? CELL_DEFER : CELL_FAIL;
-            e = K.ne;
-        }
+        rho2 = r2hi;
     }
 
     // ---- 4. output: the sorted order starts at the smallest normal angle ------

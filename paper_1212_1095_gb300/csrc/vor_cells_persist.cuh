@@ -19,6 +19,8 @@
 // (2R > rho) is handed to the second pass, which grows the disc.
 #pragma once
 
+#include <climits>
+
 #include "vor_cells_thread.cuh"
 
 namespace vor {
@@ -26,8 +28,10 @@ namespace vor {
 constexpr int P_NT = 64, P_SMAX = 16, P_EMAX = 16, P_RMAX = 32;
 constexpr int P_REFILL = 32;         // idle lanes that trigger a batched refill (all)
 // first pass: 4 sides + up to 40 sites; second pass (the cells the first
-// disc did not certify): a disc with about 2.2 times the sites, 4 + 72 entries
-constexpr int P1_CMAX = 44, P2_CMAX = 76;
+// disc did not certify): a disc with about 2.2 times the sites, 4 + 72
+// entries; third pass: the flower of the polygon an earlier pass left
+// (vor_flower.cuh), 4 + 124 entries
+constexpr int P1_CMAX = 44, P2_CMAX = 76, P3_CMAX = 128;
 
 // cp.async (sm_80+): an 8-byte copy from global to shared memory that runs
 // without registers; wait_all waits for this thread's copies only
@@ -182,6 +186,12 @@ __global__ void __launch_bounds__(NT) gather_kernel(CellParams P, GatherOut G, f
             d = rule;
             list(d);
         }
+        // a crowded disc (the density of the 3 x 3 buckets underestimates a
+        // cluster's core): a quarter of the area, up to three times
+        for (int shrink = 0; shrink < 3 && cnt > GMAX && d.rho2 > 16; shrink++) {
+            d = disc_of(g, p, d.rho2 / 4);
+            list(d);
+        }
         const i64 rho2 = d.rho2;
         G.count[t] = cnt > GMAX ? -1 : cnt;
         G.rho2[t] = rho2;
@@ -315,33 +325,48 @@ __global__ void __launch_bounds__(NT) gather_strip_kernel(CellParams P, GatherOu
         __syncthreads();
         if (mine) {
             bool direct = !staged;
-            for (int row = d.by0; row <= d.by1 && !direct; row++) {
-                int bx0, bx1;
-                if (!chord_cols(g, p, d.rho2, row, bx0, bx1)) continue;
-                if (bx0 < C0 || bx1 + 1 - C0 >= C1) { direct = true; break; }
-                const int *rb = s_bs + (row - R0) * C1;
-                const int a = rb[bx0 - C0], b = rb[bx1 + 1 - C0];
-                const int sb = s_roff[row - R0] - rb[0];        // shared index of position pos: pos + sb
-                auto take = [&](int pos, int2 q) {
-                    const int nx = q.x - p.x, ny = q.y - p.y;
-                    if (pos == t || (i64)nx * nx + (i64)ny * ny > d.rho2) return;
-                    if (cnt < GMAX) s_ent[cnt * NT + tid] = (unsigned short)(pos + sb);
-                    cnt++;
-                };
-                int pos = a;
-                for (; pos + 1 < b; pos += 2) {                  // two sites per step
-                    const int2 q0 = s_xy[pos + sb], q1 = s_xy[pos + 1 + sb];
-                    take(pos, q0);
-                    take(pos + 1, q1);
+            auto list_staged = [&]() {
+                cnt = 0;
+                for (int row = d.by0; row <= d.by1 && !direct; row++) {
+                    int bx0, bx1;
+                    if (!chord_cols(g, p, d.rho2, row, bx0, bx1)) continue;
+                    if (bx0 < C0 || bx1 + 1 - C0 >= C1) { direct = true; break; }
+                    const int *rb = s_bs + (row - R0) * C1;
+                    const int a = rb[bx0 - C0], b = rb[bx1 + 1 - C0];
+                    const int sb = s_roff[row - R0] - rb[0];    // shared index of position pos: pos + sb
+                    auto take = [&](int pos, int2 q) {
+                        const int nx = q.x - p.x, ny = q.y - p.y;
+                        if (pos == t || (i64)nx * nx + (i64)ny * ny > d.rho2) return;
+                        if (cnt < GMAX) s_ent[cnt * NT + tid] = (unsigned short)(pos + sb);
+                        cnt++;
+                    };
+                    int pos = a;
+                    for (; pos + 1 < b; pos += 2) {              // two sites per step
+                        const int2 q0 = s_xy[pos + sb], q1 = s_xy[pos + 1 + sb];
+                        take(pos, q0);
+                        take(pos + 1, q1);
+                    }
+                    if (pos < b) take(pos, s_xy[pos + sb]);
                 }
-                if (pos < b) take(pos, s_xy[pos + sb]);
-            }
-            if (direct) {
+            };
+            auto list_direct = [&]() {
                 cnt = 0;
                 for (int row = d.by0; row <= d.by1; row++) {
                     int bx0, bx1;
                     if (chord_cols(g, p, d.rho2, row, bx0, bx1)) list_global(row, bx0, bx1);
                 }
+            };
+            if (!direct) list_staged();
+            if (direct) list_direct();
+            // a crowded disc (the density of the 3 x 3 buckets underestimates
+            // a cluster's core): a quarter of the area, up to three times; the
+            // smaller disc lies inside the staged rectangle
+            for (int shrink = 0; shrink < 3 && cnt > GMAX && d.rho2 > 16; shrink++) {
+                d = disc_of(g, p, d.rho2 / 4);
+                if (!direct) list_staged();
+                if (direct) list_direct();
+            }
+            if (direct) {
                 s_cnt[tid] = -1;
             } else {
                 s_cnt[tid] = cnt;
@@ -525,6 +550,23 @@ __global__ void __launch_bounds__(NT) cells_persist_kernel(CellParams P, GatherO
                             const int q = atomicAdd(P.deferred_count, 1);
                             P.deferred[q] = i;
                             if (P.need_out) P.need_out[i] = needf;
+                            if (P.store_poly) {
+                                // a polygon the certificate could not accept:
+                                // its lines (counter-clockwise) go to the
+                                // cell's slot for the next pass's flower list
+                                // (a later polygon replaces an earlier one; a
+                                // first pass without one clears the mark)
+                                const int k = kcell;
+                                if (needf > 0.f) {
+                                    int *dst = P.slot + (size_t)k * SLOT_CAP;
+#pragma unroll
+                                    for (int q2 = 0; q2 < EMAX; q2++)
+                                        if (q2 < e) dst[q2] = lq[q2];
+                                    P.ecount[k] = -e;
+                                } else if (P.need_out) {
+                                    P.ecount[k] = 0;
+                                }
+                            }
                             cnt.deferred++;
                         } else {
                             atomicOr(&P.hdr->err, ERRB_CAPACITY);
@@ -559,7 +601,10 @@ __global__ void __launch_bounds__(NT) cells_persist_kernel(CellParams P, GatherO
                         if (P.deferred) {
                             const int q = atomicAdd(P.deferred_count, 1);
                             P.deferred[q] = i;
-                            if (P.need_out) P.need_out[i] = 0.f;
+                            if (P.need_out) {
+                                P.need_out[i] = 0.f;
+                                P.ecount[__ldg(P.sid + i)] = 0;       // no polygon
+                            }
                             cnt.deferred++;
                         } else {
                             atomicOr(&P.hdr->err, ERRB_CAPACITY);

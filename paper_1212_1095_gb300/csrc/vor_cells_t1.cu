@@ -1,5 +1,6 @@
 // vor_cells_t1.cu -- launchers of the one-thread-per-cell projector passes.
 #include "vor_cells_persist.cuh"
+#include "vor_flower.cuh"
 
 namespace vor {
 
@@ -10,7 +11,8 @@ static GatherOut gather_out(const CellParams &P, int pass, int *gcount, long lon
     // with more sites each
     const long long entries = gather_rows(P.n) * (P1_CMAX - 4);
     if (pass == 1) return GatherOut{gcount, grho2, gtab, glab, P1_CMAX - 4, P.n};
-    return GatherOut{gcount, grho2, gtab, glab, P2_CMAX - 4, (int)(entries / ((P2_CMAX - 4) * 32) * 32)};
+    const int w = pass == 2 ? P2_CMAX - 4 : P3_CMAX - 4;
+    return GatherOut{gcount, grho2, gtab, glab, w, (int)(entries / (w * 32) * 32)};
 }
 
 cudaError_t launch_gather_pass(const CellParams &P, int pass, int *gcount, long long *grho2,
@@ -22,8 +24,15 @@ cudaError_t launch_gather_pass(const CellParams &P, int pass, int *gcount, long 
             P, G, (float)P.target);
     else if (pass == 1)
         gather_kernel<64, P1_CMAX - 4, true><<<(total_max + 63) / 64, 64, 0, st>>>(P, G, (float)P.target);
-    else
+    else if (pass == 2)
         gather_kernel<128, P2_CMAX - 4, false><<<(total_max + 127) / 128, 128, 0, st>>>(P, G, 2.2f * (float)P.target);
+    else {
+        // one warp per cell of the list; a grid of a few warps per SM slot,
+        // the rest by grid stride (the list length is known on the device)
+        const long long want = ((long long)total_max + FL_WARPS - 1) / FL_WARPS;
+        const int grid = (int)(want < 152 * 16 ? (want > 0 ? want : 1) : 152 * 16);
+        flower_gather_kernel<P3_CMAX - 4><<<grid, 32 * FL_WARPS, 0, st>>>(P, G);
+    }
     return cudaGetLastError();
 }
 
@@ -46,7 +55,9 @@ static cudaError_t launch_persist(const CellParams &P, const GatherOut &G, cudaS
 cudaError_t launch_cells_pass(const CellParams &P, int pass, int *gcount, long long *grho2,
                               float2 *gtab, int *glab, cudaStream_t st) {
     const GatherOut G = gather_out(P, pass, gcount, grho2, gtab, glab);
-    return pass == 1 ? launch_persist<P1_CMAX>(P, G, st) : launch_persist<P2_CMAX>(P, G, st);
+    if (pass == 1) return launch_persist<P1_CMAX>(P, G, st);
+    if (pass == 2) return launch_persist<P2_CMAX>(P, G, st);
+    return launch_persist<P3_CMAX>(P, G, st);
 }
 
 int pass_gather_width() { return P1_CMAX - 4; }

@@ -1,0 +1,227 @@
+// vor_flower.cuh -- the flower gather of the third thread-per-cell pass:
+// one warp lists the candidates of one cell from the polygon an earlier pass
+// left in the cell's slot.
+//
+// A site a cuts a convex polygon P around p exactly when it lies strictly
+// inside the disc of some vertex w of P through p: |x - p|^2 - |x - a|^2 is
+// affine in x, so its maximum over P is reached at a vertex.  (The sites of
+// P's own edges lie on such circles.)  The polygon's "flower" (the union of
+// these discs) therefore holds every site that can still change the cell;
+// the farther sites are never needed (the argument of Lemmas Byy'Syy' and
+// SitesInLargeSquare, with the vertex discs in place of the disc of radius
+// 2R).
+//
+// The warp reads the bucket rows that meet the flower (lanes over rows, a
+// prefix sum over the row ranges so that every lane takes sites), tests each
+// site against the vertex discs (a float test with a margin: a superset),
+// and histograms the distances of the flower's sites from p.  When all of
+// them fit the list, the list is complete: the cell among the listed sites
+// is the Voronoi cell, and its certificate radius is unbounded.  Otherwise
+// the list takes the flower's sites nearest to p up to a distance rho that
+// fits, and the usual certificate 2R <= rho decides: every site within rho
+// that could cut is listed, and the ones that cannot cut P cannot cut the
+// smaller polygon computed from the list either.
+#pragma once
+
+#include <climits>
+
+#include "vor_cells.cuh"
+#include "vor_cells_persist.cuh"
+
+namespace vor {
+
+constexpr int FL_WARPS = 4;            // warps per block
+constexpr int FL_ROWS = 256;           // bucket rows a flower may span
+constexpr int FL_SITES = 2048;         // sites its row ranges may hold (else the next tier)
+
+// The line of label lab (a site of the cell's set, or a side -1..-4) in the
+// cell of p: 2 <n, v - p> = c.
+__device__ __forceinline__ void label_line(const CellParams &P, const CellGrid &g, int2 p, int lab,
+                                           int &nx, int &ny, i64 &c) {
+    if (lab >= 0) {
+        const int2 a = __ldg(P.sites + g.site_base + lab);
+        nx = a.x - p.x;
+        ny = a.y - p.y;
+        c = (i64)nx * nx + (i64)ny * ny;
+        return;
+    }
+    nx = ny = 0;
+    if (lab == VOR_SIDE_BOTTOM) ny = -p.y;
+    else if (lab == VOR_SIDE_RIGHT) nx = g.W - p.x;
+    else if (lab == VOR_SIDE_TOP) ny = g.H - p.y;
+    else nx = -p.x;
+    c = 2 * ((i64)nx * nx + (i64)ny * ny);
+}
+
+struct FlowerSmem {
+    float wx[SLOT_CAP], wy[SLOT_CAP], wr[SLOT_CAP];   // vertices relative to p, padded radii
+    int hist[32];
+    int cnt;
+};
+
+// does the site n = a - p lie inside or on (with a margin) a vertex disc?
+__device__ __forceinline__ bool in_flower(const FlowerSmem &F, int e, int nx, int ny) {
+    const float fnx = (float)nx, fny = (float)ny;
+    const float nn = fmaf(fnx, fnx, fny * fny);
+    for (int q = 0; q < e; q++) {
+        const float px = fnx * F.wx[q], py = fny * F.wy[q];
+        const float f = 2.f * (px + py) - nn;
+        const float mg = 0x1p-16f * (2.f * (fabsf(px) + fabsf(py)) + nn) + 1.f;
+        if (f > -mg) return true;
+    }
+    return false;
+}
+
+template <int GMAX>
+__global__ void __launch_bounds__(32 * FL_WARPS) flower_gather_kernel(CellParams P, GatherOut G) {
+    __shared__ FlowerSmem sm[FL_WARPS];
+    if (P.hdr->err) return;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    FlowerSmem &F = sm[wib];
+    const int listed = *P.list_count;
+    const int total = min(listed, G.cap);
+    const int nwarps = gridDim.x * FL_WARPS;
+    for (int t = G.cap + blockIdx.x * blockDim.x + threadIdx.x; t < listed; t += gridDim.x * blockDim.x)
+        G.count[t] = -1;                                   // beyond the lists: the next tier
+    for (int t = blockIdx.x * FL_WARPS + wib; t < total; t += nwarps) {
+        const int i = P.cell_list[t];
+        const int2 p = P.sxy[i];
+        const CellGrid g = cell_grid(P, i);
+        const int k = __ldg(P.sid + i);
+        const int e1 = -P.ecount[k];
+        if (e1 < 3 || e1 > SLOT_CAP) {                     // no polygon: the next tier
+            if (lane == 0) { G.count[t] = -1; G.rho2[t] = 0; }
+            continue;
+        }
+        // the polygon's lines, one per lane, then vertex q = lines q and q + 1
+        int nx = 0, ny = 0;
+        i64 c = 0;
+        if (lane < e1) label_line(P, g, p, P.slot[(size_t)k * SLOT_CAP + lane], nx, ny, c);
+        const int src = lane + 1 < e1 ? lane + 1 : 0;
+        const int n2x = __shfl_sync(FULL, nx, src), n2y = __shfl_sync(FULL, ny, src);
+        const i64 c2 = __shfl_sync(FULL, c, src);
+        float ylo = FLT_MAX, yhi = -FLT_MAX, r2max = 0.f;
+        int bad = 0;
+        if (lane < e1) {
+            i64 Nx, Ny, D;
+            intersect(nx, ny, c, n2x, n2y, c2, Nx, Ny, D);
+            if (D == 0) {
+                bad = 1;
+            } else {
+                const float rd = 1.f / (float)D;
+                const float wx = (float)Nx * rd, wy = (float)Ny * rd;
+                // radius through p, padded for the float vertex
+                const float wr = sqrtf(fmaf(wx, wx, wy * wy)) * (1.f + 0x1p-10f) + 2.f;
+                F.wx[lane] = wx;
+                F.wy[lane] = wy;
+                F.wr[lane] = wr;
+                ylo = (float)p.y + wy - wr;
+                yhi = (float)p.y + wy + wr;
+                const float far = sqrtf(fmaf(wx, wx, wy * wy)) + wr;   // farthest flower point from p
+                r2max = far * far;
+            }
+        }
+        F.hist[lane] = 0;
+        if (lane == 0) F.cnt = 0;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            ylo = fminf(ylo, __shfl_xor_sync(FULL, ylo, off));
+            yhi = fmaxf(yhi, __shfl_xor_sync(FULL, yhi, off));
+            r2max = fmaxf(r2max, __shfl_xor_sync(FULL, r2max, off));
+            bad |= __shfl_xor_sync(FULL, bad, off);
+        }
+        const int s = g.s;
+        const int by0 = max(0, (int)floorf(ylo / (float)s));
+        const int by1 = min(g.m2 - 1, (int)floorf(yhi / (float)s));
+        if (bad || by1 - by0 >= FL_ROWS) {
+            if (lane == 0) { G.count[t] = -1; G.rho2[t] = 0; }
+            continue;
+        }
+        __syncwarp();
+        // the row ranges meeting the flower: the union of the vertex discs'
+        // chords over the row's band
+        auto span = [&](int row, int *x0, int *x1) -> int {
+            const float fy0 = (float)row * (float)s, fy1 = fy0 + (float)s;
+            float xlo = FLT_MAX, xhi = -FLT_MAX;
+            for (int q = 0; q < e1; q++) {
+                const float cy = (float)p.y + F.wy[q];
+                const float dv = fmaxf(0.f, fmaxf(fy0 - cy, cy - fy1));
+                if (dv > F.wr[q]) continue;
+                const float h = sqrtf(fmaxf(F.wr[q] * F.wr[q] - dv * dv, 0.f)) + 1.f;
+                const float cx = (float)p.x + F.wx[q];
+                xlo = fminf(xlo, cx - h);
+                xhi = fmaxf(xhi, cx + h);
+            }
+            if (xlo > xhi) return 0;
+            x0[0] = max(0, (int)floorf(fmaxf(xlo, -1.f) / (float)s));
+            x1[0] = min(g.m1 - 1, (int)floorf(fminf(xhi, (float)g.W + 1.f) / (float)s));
+            return x0[0] <= x1[0] ? 1 : 0;
+        };
+        // the sites the row ranges hold: a flower over crowded buckets goes
+        // to the next tier (whose certificate grows the region gradually)
+        // without being read
+        int held = 0;
+        for (int r0 = by0; r0 <= by1; r0 += 32) {
+            const int row = r0 + lane;
+            int x0, x1;
+            if (row <= by1 && span(row, &x0, &x1))
+                held += g.bs[row * g.m1 + x1 + 1] - g.bs[row * g.m1 + x0];
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) held += __shfl_xor_sync(FULL, held, off);
+        if (held > FL_SITES) {
+            if (lane == 0) { G.count[t] = -1; G.rho2[t] = 0; }
+            __syncwarp();
+            continue;
+        }
+        // pass 1: the flower's sites by distance from p (32 bins of |a - p|^2)
+        const float binscale = 32.f / fmaxf(r2max, 1.f);
+        auto count = [&](int pos, int2 q) {
+            if (pos == i) return;
+            const int ax = q.x - p.x, ay = q.y - p.y;
+            if (!in_flower(F, e1, ax, ay)) return;
+            const float d2 = (float)((i64)ax * ax + (i64)ay * ay);
+            atomicAdd(&F.hist[min(31, (int)(d2 * binscale))], 1);
+        };
+        scan_rows<32, 1, 2>(g, P.sxy, by0, by1, lane, FULL, span, count);
+        __syncwarp();
+        // the nearest bins that fit: all of them (a complete list), or those
+        // below bin b (every flower site with |a - p|^2 < b r2max / 32)
+        int b = 0, sum = 0;
+        while (b < 32 && sum + F.hist[b] <= GMAX) sum += F.hist[b++];
+        i64 lim2 = LLONG_MAX;                                  // list |a - p|^2 < lim2
+        i64 rho2 = LLONG_MAX;                                  // certificate radius
+        if (b < 32) {
+            // integer threshold below the float bin edge: the listed sites
+            // are those with d2 < lim2, a superset-free subset of the bins
+            lim2 = (i64)((float)b / binscale);
+            rho2 = lim2 - 1;
+            if (rho2 < 1) {
+                if (lane == 0) { G.count[t] = -1; G.rho2[t] = 0; }
+                continue;
+            }
+        }
+        // pass 2: list them (entry order does not change the cell)
+        auto list = [&](int pos, int2 q) {
+            if (pos == i) return;
+            const int ax = q.x - p.x, ay = q.y - p.y;
+            if ((i64)ax * ax + (i64)ay * ay >= lim2 || !in_flower(F, e1, ax, ay)) return;
+            const int at = atomicAdd(&F.cnt, 1);
+            if (at < GMAX) {
+                G.tab[G.at(t, at)] = t1::cand_of(ax, ay);
+                G.lab[G.at(t, at)] = __ldg(P.sid + pos) - g.site_base;
+            }
+        };
+        scan_rows<32, 1, 2>(g, P.sxy, by0, by1, lane, FULL, span, list);
+        __syncwarp();
+        if (lane == 0) {
+            const int n_list = F.cnt;
+            G.count[t] = n_list <= GMAX ? n_list : -1;
+            G.rho2[t] = rho2;
+        }
+        __syncwarp();
+    }
+}
+
+}  // namespace vor

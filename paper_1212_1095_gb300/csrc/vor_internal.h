@@ -36,10 +36,12 @@ struct WsHeader {
     int m_total;            // buckets over all sets (set by the grid choice)
     int ndeferred3;         // cells handed from the medium tier to the block-per-cell tier
     int coop_next;          // next cell of the block-per-cell tier (shared-memory mode)
-    int pass_next[2];       // next list entry of the two thread-per-cell passes
+    int pass_next[3];       // next list entry of the three thread-per-cell passes
     int ndeferred4;         // cells handed on to the global-memory mode of that tier
     int coop_next2;         // next cell of the global-memory mode
-    long long pad[8];
+    int ndeferred5;         // cells handed from the third thread-per-cell pass to the medium tier
+    int three_pass;         // 1: the three thread-per-cell passes ran (set by a memset)
+    long long pad[7];
 };
 static_assert(sizeof(WsHeader) <= 256, "header");
 
@@ -131,6 +133,8 @@ struct CellParams {
     float *need_out;        // first pass: per deferred cell (by sorted position) the
                             // squared disc radius its polygon needs, 0 when unknown
     const float *need_in;   // second pass: the same, read by its gather
+    int store_poly;         // thread-per-cell passes: a cell whose polygon the certificate
+                            // cannot accept leaves its lines in its slot (ecount = -e)
     WsHeader *hdr;
 };
 

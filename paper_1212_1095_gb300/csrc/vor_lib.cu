@@ -712,8 +712,8 @@ struct Layout {
     int s_fixed, lanes, target, n_sets, load_pct;
     long long n, m_sum, g_sum;
     size_t hdr, sets, sset, bstart, rank, sxy, sid, partial, ecount, dcount, loc, del_ptr, slot,
-        spill, deferred, deferred2, deferred3, deferred4, gcount, grho2, gtab, glab, coarse, coop,
-        total;
+        spill, deferred, deferred2, deferred3, deferred4, deferred5, gcount, grho2, gtab, glab, coarse,
+        coop, total;
     int spill_cap;
     int n_partial;
     long long n_max;          // largest set
@@ -796,6 +796,7 @@ static bool resolve(const int64_t *set_ptr, const vor_box *boxes, int n_sets, in
     L.deferred2 = at; at = align256(at + nn * 4);
     L.deferred3 = at; at = align256(at + nn * 4);
     L.deferred4 = at; at = align256(at + nn * 4);
+    L.deferred5 = at; at = align256(at + nn * 4);
     L.gcount = at;   at = align256(at + nn * 4);
     L.grho2 = at;    at = align256(at + nn * 8);
     L.gtab = at;     at = align256(at + (size_t)gather_rows(nn) * 8 * (size_t)pass_gather_width());
@@ -855,6 +856,7 @@ static int launch_build(const BatchArgs &A, const vor_opts *o, void *ws, const L
     int *deferred2 = (int *)(base + L.deferred2);
     int *deferred3 = (int *)(base + L.deferred3);
     int *deferred4 = (int *)(base + L.deferred4);
+    int *deferred5 = (int *)(base + L.deferred5);
     int *coarse = (int *)(base + L.coarse);
     const int2 *sites = A.sites;
 
@@ -914,6 +916,7 @@ static int launch_build(const BatchArgs &A, const vor_opts *o, void *ws, const L
     P.spill_cap = L.spill_cap;
     P.cell_list = nullptr; P.list_count = nullptr; P.n_list = 0;
     P.hdr = hdr;
+    int *med_list = deferred2, *med_count = &hdr->ndeferred2;   // the medium tier's cells
     if (L.lanes == 1) {
         int *gcount = (int *)(base + L.gcount), *glab = (int *)(base + L.glab);
         float2 *gtab = (float2 *)(base + L.gtab);
@@ -925,6 +928,7 @@ static int launch_build(const BatchArgs &A, const vor_opts *o, void *ws, const L
         // the bucket ranks are free after bucketing: they carry the first
         // pass's disc needs to the second pass
         P.need_out = (float *)rank;
+        P.store_poly = 1;
         if (launch_gather_pass(P, 1, gcount, grho2, gtab, glab, st) != cudaSuccess) return VOR_E_CUDA;
         mark(2, st);
         CellParams P1 = P;
@@ -943,7 +947,23 @@ static int launch_build(const BatchArgs &A, const vor_opts *o, void *ws, const L
         if (launch_gather_pass(P2, 2, gcount, grho2, gtab, glab, st) != cudaSuccess) return VOR_E_CUDA;
         P2.next_cell = &hdr->pass_next[1];
         if (launch_cells_pass(P2, 2, gcount, grho2, gtab, glab, st) != cudaSuccess) return VOR_E_CUDA;
-        launched += 4;                // two gathers, two persistent passes
+        // third pass: the flower of the polygon the second (or first) pass
+        // left, when it fits 124 entries; the rest goes to the medium tier
+        CellParams P3 = P2;
+        P3.cell_list = deferred2;
+        P3.list_count = &hdr->ndeferred2;
+        P3.deferred = deferred5;
+        P3.deferred_count = &hdr->ndeferred5;
+        P3.need_in = nullptr;
+        P3.store_poly = 0;
+        P3.next_cell = nullptr;
+        if (launch_gather_pass(P3, 3, gcount, grho2, gtab, glab, st) != cudaSuccess) return VOR_E_CUDA;
+        P3.next_cell = &hdr->pass_next[2];
+        if (launch_cells_pass(P3, 3, gcount, grho2, gtab, glab, st) != cudaSuccess) return VOR_E_CUDA;
+        med_list = deferred5;
+        med_count = &hdr->ndeferred5;
+        if (cudaMemsetAsync(&hdr->three_pass, 1, 1, st) != cudaSuccess) return VOR_E_CUDA;
+        launched += 6;                // three gathers, three persistent passes
         mark(4, st);
     } else {
         P.deferred = deferred2;
@@ -960,8 +980,9 @@ static int launch_build(const BatchArgs &A, const vor_opts *o, void *ws, const L
     CellParams PM = P;
     PM.need_out = nullptr;
     PM.need_in = nullptr;
-    PM.cell_list = deferred2;
-    PM.list_count = &hdr->ndeferred2;
+    PM.store_poly = 0;
+    PM.cell_list = med_list;
+    PM.list_count = med_count;
     PM.n_list = n;
     PM.deferred = deferred3;
     PM.deferred_count = &hdr->ndeferred3;
@@ -1152,7 +1173,10 @@ int vor_status(const void *d_workspace, void *stream, vor_stats *stats) {
         stats->evals_first_pass = h.stats[STAT_EVALS1];
         stats->rays_first_pass = h.stats[STAT_RAYS1];
         stats->evals_second_pass = h.stats[STAT_EVALS2];
-        stats->medium_cells = (uint64_t)(h.ndeferred2 > 0 ? h.ndeferred2 : 0);
+        const int third = h.three_pass ? h.ndeferred2 : 0;
+        const int medium = h.three_pass ? h.ndeferred5 : h.ndeferred2;
+        stats->third_pass_cells = (uint64_t)(third > 0 ? third : 0);
+        stats->medium_cells = (uint64_t)(medium > 0 ? medium : 0);
         stats->large_cells = (uint64_t)(h.ndeferred3 > 0 ? h.ndeferred3 : 0);
         stats->global_cells = (uint64_t)(h.ndeferred4 > 0 ? h.ndeferred4 : 0);
     }
