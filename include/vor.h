@@ -99,7 +99,7 @@ typedef struct vor_stats {
     uint64_t evals_first_pass; /* the part of evals done by the first thread-per-cell pass */
     uint64_t rays_first_pass;  /* the part of rays shot by the first thread-per-cell pass  */
     uint64_t evals_second_pass;/* the part of evals done by the second thread-per-cell pass*/
-    uint64_t third_pass_cells; /* cells handed to the third thread-per-cell pass           */
+    uint64_t third_pass_cells; /* cells handed to the thread-per-cell flower passes        */
     uint64_t medium_cells;     /* cells handed to the warp-per-cell medium tier            */
     uint64_t large_cells;      /* cells handed on to the block-per-cell tier               */
     uint64_t global_cells;     /* of those, cells too large for its shared-memory mode     */

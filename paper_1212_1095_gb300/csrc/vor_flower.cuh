@@ -11,16 +11,19 @@
 // SitesInLargeSquare, with the vertex discs in place of the disc of radius
 // 2R).
 //
-// The warp reads the bucket rows that meet the flower (lanes over rows, a
-// prefix sum over the row ranges so that every lane takes sites), tests each
-// site against the vertex discs (a float test with a margin: a superset),
-// and histograms the distances of the flower's sites from p.  When all of
-// them fit the list, the list is complete: the cell among the listed sites
+// The warp reads the bucket rows that meet the flower, nearest p first and
+// within a budget of sites (lanes over rows, a prefix sum over the row
+// ranges so that every lane takes sites), tests each site against the
+// vertex discs (a float test with a margin: a superset), and histograms the
+// distances of the flower's sites from p.  When the whole flower was read
+// and fits the list, the list is complete: the cell among the listed sites
 // is the Voronoi cell, and its certificate radius is unbounded.  Otherwise
 // the list takes the flower's sites nearest to p up to a distance rho that
-// fits, and the usual certificate 2R <= rho decides: every site within rho
-// that could cut is listed, and the ones that cannot cut P cannot cut the
-// smaller polygon computed from the list either.
+// fits (and that the rows read cover), and the usual certificate 2R <= rho
+// decides: every site within rho that could cut is listed, and the ones that
+// cannot cut P cannot cut the smaller polygon computed from the list either.
+// A cell the certificate does not accept leaves its new polygon for the
+// next flower pass.
 #pragma once
 
 #include <climits>
@@ -32,7 +35,12 @@ namespace vor {
 
 constexpr int FL_WARPS = 4;            // warps per block
 constexpr int FL_ROWS = 256;           // bucket rows a flower may span
-constexpr int FL_SITES = 2048;         // sites its row ranges may hold (else the next tier)
+constexpr int FL_SITES = 2048;         // sites the rows read may hold
+// Below this many cells the pass is left out (every cell goes to the warp
+// tier): a few cells of up to 124 candidates each on one thread take longer
+// than the same cells spread over the lanes of a warp; the pass pays off
+// when its cells fill the GPU.
+constexpr int FL_MIN_CELLS = 16384;
 
 // The line of label lab (a site of the cell's set, or a side -1..-4) in the
 // cell of p: 2 <n, v - p> = c.
@@ -57,6 +65,7 @@ struct FlowerSmem {
     float wx[SLOT_CAP], wy[SLOT_CAP], wr[SLOT_CAP];   // vertices relative to p, padded radii
     int hist[32];
     int cnt;
+    int held[FL_ROWS];                                 // sites in each row's range
 };
 
 // does the site n = a - p lie inside or on (with a margin) a vertex disc?
@@ -80,9 +89,9 @@ __global__ void __launch_bounds__(32 * FL_WARPS) flower_gather_kernel(CellParams
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     FlowerSmem &F = sm[wib];
     const int listed = *P.list_count;
-    const int total = min(listed, G.cap);
+    const int total = listed < FL_MIN_CELLS ? 0 : min(listed, G.cap);
     const int nwarps = gridDim.x * FL_WARPS;
-    for (int t = G.cap + blockIdx.x * blockDim.x + threadIdx.x; t < listed; t += gridDim.x * blockDim.x)
+    for (int t = total + blockIdx.x * blockDim.x + threadIdx.x; t < listed; t += gridDim.x * blockDim.x)
         G.count[t] = -1;                                   // beyond the lists: the next tier
     for (int t = blockIdx.x * FL_WARPS + wib; t < total; t += nwarps) {
         const int i = P.cell_list[t];
@@ -132,12 +141,21 @@ __global__ void __launch_bounds__(32 * FL_WARPS) flower_gather_kernel(CellParams
             bad |= __shfl_xor_sync(FULL, bad, off);
         }
         const int s = g.s;
-        const int by0 = max(0, (int)floorf(ylo / (float)s));
-        const int by1 = min(g.m2 - 1, (int)floorf(yhi / (float)s));
-        if (bad || by1 - by0 >= FL_ROWS) {
+        const int prow = p.y / s;
+        // the rows of the flower, at most FL_ROWS of them around p's row
+        int by0 = max(0, (int)floorf(ylo / (float)s));
+        int by1 = min(g.m2 - 1, (int)floorf(yhi / (float)s));
+        by0 = max(by0, prow - FL_ROWS / 2 + 1);
+        by1 = min(by1, prow + FL_ROWS / 2);
+        if (bad) {
             if (lane == 0) { G.count[t] = -1; G.rho2[t] = 0; }
             continue;
         }
+        // distance from p to the band of a row (0 for p's own row)
+        auto row_dist = [&](int row) -> float {
+            return row > prow ? (float)row * (float)s - (float)p.y
+                              : (row < prow ? (float)p.y - (float)(row + 1) * (float)s : 0.f);
+        };
         __syncwarp();
         // the row ranges meeting the flower: the union of the vertex discs'
         // chords over the row's band
@@ -158,31 +176,70 @@ __global__ void __launch_bounds__(32 * FL_WARPS) flower_gather_kernel(CellParams
             x1[0] = min(g.m1 - 1, (int)floorf(fminf(xhi, (float)g.W + 1.f) / (float)s));
             return x0[0] <= x1[0] ? 1 : 0;
         };
-        // the sites the row ranges hold: a flower over crowded buckets goes
-        // to the next tier (whose certificate grows the region gradually)
-        // without being read
-        int held = 0;
+        // the sites each row's range holds; the rows nearest p (in order of
+        // |row - prow|) are read while they hold at most FL_SITES sites in
+        // all, and the radius rt is the distance from p to the nearest row
+        // left out (or cut off by the FL_ROWS window): every site closer to p
+        // than rt lies in the rows read
         for (int r0 = by0; r0 <= by1; r0 += 32) {
             const int row = r0 + lane;
             int x0, x1;
-            if (row <= by1 && span(row, &x0, &x1))
-                held += g.bs[row * g.m1 + x1 + 1] - g.bs[row * g.m1 + x0];
+            if (row <= by1)
+                F.held[row - by0] = span(row, &x0, &x1) ? g.bs[row * g.m1 + x1 + 1] - g.bs[row * g.m1 + x0] : 0;
         }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) held += __shfl_xor_sync(FULL, held, off);
-        if (held > FL_SITES) {
+        __syncwarp();
+        int lo = prow, hi = prow - 1;                      // rows read: [lo, hi]
+        {
+            int sum = 0;
+            for (int kk = 0;; kk++) {
+                const int h = (kk + 1) >> 1;
+                const int row = (kk & 1) ? prow + h : prow - h;
+                if (h > FL_ROWS) break;
+                if (row < by0 || row > by1) {
+                    if (prow + h > by1 && prow - h < by0) break;
+                    continue;
+                }
+                const int add = F.held[row - by0];
+                if (sum + add > FL_SITES) break;
+                sum += add;
+                lo = min(lo, row);
+                hi = max(hi, row);
+            }
+        }
+        float rt = FLT_MAX;
+        if (hi >= lo) {
+            // rows beyond [lo, hi] that the flower reaches, or the window cut
+            const int top = min(g.m2 - 1, (int)floorf(yhi / (float)s));
+            const int bot = max(0, (int)floorf(ylo / (float)s));
+            if (hi < top) rt = fminf(rt, row_dist(hi + 1));
+            if (lo > bot) rt = fminf(rt, row_dist(lo - 1));
+        }
+        if (hi < lo || rt < 1.f) {                         // not even p's own row fits
             if (lane == 0) { G.count[t] = -1; G.rho2[t] = 0; }
             __syncwarp();
             continue;
+        }
+        by0 = lo;
+        by1 = hi;
+        // the listed sites lie closer than sqrt(lim2) (integer, at most rt^2)
+        i64 lim2 = LLONG_MAX;
+        if (rt < FLT_MAX) {
+            lim2 = (i64)(rt * rt * (1.f - 0x1p-20f));
+            if (lim2 < 2) {
+                if (lane == 0) { G.count[t] = -1; G.rho2[t] = 0; }
+                __syncwarp();
+                continue;
+            }
+            r2max = fminf(r2max, (float)lim2);
         }
         // pass 1: the flower's sites by distance from p (32 bins of |a - p|^2)
         const float binscale = 32.f / fmaxf(r2max, 1.f);
         auto count = [&](int pos, int2 q) {
             if (pos == i) return;
             const int ax = q.x - p.x, ay = q.y - p.y;
-            if (!in_flower(F, e1, ax, ay)) return;
-            const float d2 = (float)((i64)ax * ax + (i64)ay * ay);
-            atomicAdd(&F.hist[min(31, (int)(d2 * binscale))], 1);
+            const i64 dd = (i64)ax * ax + (i64)ay * ay;
+            if (dd >= lim2 || !in_flower(F, e1, ax, ay)) return;
+            atomicAdd(&F.hist[min(31, (int)((float)dd * binscale))], 1);
         };
         scan_rows<32, 1, 2>(g, P.sxy, by0, by1, lane, FULL, span, count);
         __syncwarp();
@@ -190,17 +247,13 @@ __global__ void __launch_bounds__(32 * FL_WARPS) flower_gather_kernel(CellParams
         // below bin b (every flower site with |a - p|^2 < b r2max / 32)
         int b = 0, sum = 0;
         while (b < 32 && sum + F.hist[b] <= GMAX) sum += F.hist[b++];
-        i64 lim2 = LLONG_MAX;                                  // list |a - p|^2 < lim2
-        i64 rho2 = LLONG_MAX;                                  // certificate radius
-        if (b < 32) {
-            // integer threshold below the float bin edge: the listed sites
-            // are those with d2 < lim2, a superset-free subset of the bins
-            lim2 = (i64)((float)b / binscale);
-            rho2 = lim2 - 1;
-            if (rho2 < 1) {
-                if (lane == 0) { G.count[t] = -1; G.rho2[t] = 0; }
-                continue;
-            }
+        if (b < 32) lim2 = min(lim2, (i64)((float)b / binscale));   // the bins below b
+        // certificate radius: unbounded when the whole flower is listed, else
+        // every flower site with |a - p|^2 <= rho2 is listed
+        const i64 rho2 = lim2 == LLONG_MAX ? LLONG_MAX : lim2 - 1;
+        if (rho2 < 1) {
+            if (lane == 0) { G.count[t] = -1; G.rho2[t] = 0; }
+            continue;
         }
         // pass 2: list them (entry order does not change the cell)
         auto list = [&](int pos, int2 q) {

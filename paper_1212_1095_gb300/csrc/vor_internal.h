@@ -25,6 +25,9 @@ enum {
     STAT_DEFERRED, STAT_CANDIDATES, STAT_MAXE, STAT_WIDEN, STAT_EVALS1, STAT_RAYS1, STAT_EVALS2, STAT_N = 16
 };
 
+// Thread-per-cell passes over the flower of the polygon an earlier pass left.
+constexpr int FLOWER_PASSES = 3;
+
 // Workspace header (first 256 bytes of the workspace).
 struct WsHeader {
     unsigned err;
@@ -36,17 +39,19 @@ struct WsHeader {
     int m_total;            // buckets over all sets (set by the grid choice)
     int ndeferred3;         // cells handed from the medium tier to the block-per-cell tier
     int coop_next;          // next cell of the block-per-cell tier (shared-memory mode)
-    int pass_next[3];       // next list entry of the three thread-per-cell passes
+    int pass_next[2];       // next list entry of the first two thread-per-cell passes
     int ndeferred4;         // cells handed on to the global-memory mode of that tier
     int coop_next2;         // next cell of the global-memory mode
-    int ndeferred5;         // cells handed from the third thread-per-cell pass to the medium tier
-    int three_pass;         // 1: the three thread-per-cell passes ran (set by a memset)
-    long long pad[7];
+    int flower_passes;      // flower passes that ran (set by a memset; 0: none)
+    int fcount[FLOWER_PASSES];  // cells each flower pass hands on
+    int fnext[FLOWER_PASSES];   // next list entry of each flower pass
+    long long pad[4];
 };
 static_assert(sizeof(WsHeader) <= 256, "header");
 
 // Cells a first-pass group stores in fixed slots (larger ones spill).
 constexpr int SLOT_CAP = 16;
+
 
 // One point set of a batch (a single build is a batch of one set).
 struct SetMeta {

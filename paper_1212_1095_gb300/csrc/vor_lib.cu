@@ -796,7 +796,7 @@ static bool resolve(const int64_t *set_ptr, const vor_box *boxes, int n_sets, in
     L.deferred2 = at; at = align256(at + nn * 4);
     L.deferred3 = at; at = align256(at + nn * 4);
     L.deferred4 = at; at = align256(at + nn * 4);
-    L.deferred5 = at; at = align256(at + nn * 4);
+    L.deferred5 = at; at = align256(at + nn * 4);   // flower passes alternate with deferred2
     L.gcount = at;   at = align256(at + nn * 4);
     L.grho2 = at;    at = align256(at + nn * 8);
     L.gtab = at;     at = align256(at + (size_t)gather_rows(nn) * 8 * (size_t)pass_gather_width());
@@ -947,23 +947,31 @@ static int launch_build(const BatchArgs &A, const vor_opts *o, void *ws, const L
         if (launch_gather_pass(P2, 2, gcount, grho2, gtab, glab, st) != cudaSuccess) return VOR_E_CUDA;
         P2.next_cell = &hdr->pass_next[1];
         if (launch_cells_pass(P2, 2, gcount, grho2, gtab, glab, st) != cudaSuccess) return VOR_E_CUDA;
-        // third pass: the flower of the polygon the second (or first) pass
-        // left, when it fits 124 entries; the rest goes to the medium tier
-        CellParams P3 = P2;
-        P3.cell_list = deferred2;
-        P3.list_count = &hdr->ndeferred2;
-        P3.deferred = deferred5;
-        P3.deferred_count = &hdr->ndeferred5;
-        P3.need_in = nullptr;
-        P3.store_poly = 0;
-        P3.next_cell = nullptr;
-        if (launch_gather_pass(P3, 3, gcount, grho2, gtab, glab, st) != cudaSuccess) return VOR_E_CUDA;
-        P3.next_cell = &hdr->pass_next[2];
-        if (launch_cells_pass(P3, 3, gcount, grho2, gtab, glab, st) != cudaSuccess) return VOR_E_CUDA;
-        med_list = deferred5;
-        med_count = &hdr->ndeferred5;
-        if (cudaMemsetAsync(&hdr->three_pass, 1, 1, st) != cudaSuccess) return VOR_E_CUDA;
-        launched += 6;                // three gathers, three persistent passes
+        // flower passes: the flower of the polygon an earlier pass left, its
+        // sites nearest p first, up to 124 entries; a cell its certificate
+        // does not accept leaves the new polygon for the next flower pass,
+        // and what is left after the last goes to the medium tier
+        int *fin = deferred2, *fin_count = &hdr->ndeferred2;
+        for (int f = 0; f < FLOWER_PASSES; f++) {
+            int *fout = (f & 1) ? deferred2 : deferred5;
+            CellParams P3 = P2;
+            P3.cell_list = fin;
+            P3.list_count = fin_count;
+            P3.deferred = fout;
+            P3.deferred_count = &hdr->fcount[f];
+            P3.need_in = nullptr;
+            P3.store_poly = 1;
+            P3.next_cell = nullptr;
+            if (launch_gather_pass(P3, 3, gcount, grho2, gtab, glab, st) != cudaSuccess) return VOR_E_CUDA;
+            P3.next_cell = &hdr->fnext[f];
+            if (launch_cells_pass(P3, 3, gcount, grho2, gtab, glab, st) != cudaSuccess) return VOR_E_CUDA;
+            fin = fout;
+            fin_count = &hdr->fcount[f];
+        }
+        med_list = fin;
+        med_count = fin_count;
+        if (cudaMemsetAsync(&hdr->flower_passes, FLOWER_PASSES, 1, st) != cudaSuccess) return VOR_E_CUDA;
+        launched += 4 + 2 * FLOWER_PASSES;
         mark(4, st);
     } else {
         P.deferred = deferred2;
@@ -1173,8 +1181,8 @@ int vor_status(const void *d_workspace, void *stream, vor_stats *stats) {
         stats->evals_first_pass = h.stats[STAT_EVALS1];
         stats->rays_first_pass = h.stats[STAT_RAYS1];
         stats->evals_second_pass = h.stats[STAT_EVALS2];
-        const int third = h.three_pass ? h.ndeferred2 : 0;
-        const int medium = h.three_pass ? h.ndeferred5 : h.ndeferred2;
+        const int third = h.flower_passes ? h.ndeferred2 : 0;
+        const int medium = h.flower_passes ? h.fcount[h.flower_passes - 1] : h.ndeferred2;
         stats->third_pass_cells = (uint64_t)(third > 0 ? third : 0);
         stats->medium_cells = (uint64_t)(medium > 0 ? medium : 0);
         stats->large_cells = (uint64_t)(h.ndeferred3 > 0 ? h.ndeferred3 : 0);
