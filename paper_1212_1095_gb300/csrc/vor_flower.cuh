@@ -35,7 +35,7 @@ namespace vor {
 
 constexpr int FL_WARPS = 4;            // warps per block
 constexpr int FL_ROWS = 256;           // bucket rows a flower may span
-constexpr int FL_SITES = 2048;         // sites the rows read may hold
+constexpr int FL_SITES = 1024;         // sites the rows read may hold
 // Below this many cells the pass is left out (every cell goes to the warp
 // tier): a few cells of up to 124 candidates each on one thread take longer
 // than the same cells spread over the lanes of a warp; the pass pays off
@@ -66,13 +66,17 @@ struct FlowerSmem {
     int hist[32];
     int cnt;
     int held[FL_ROWS];                                 // sites in each row's range
+    unsigned short disc[FL_ROWS];                      // vertex discs meeting each row's band
 };
 
-// does the site n = a - p lie inside or on (with a margin) a vertex disc?
-__device__ __forceinline__ bool in_flower(const FlowerSmem &F, int e, int nx, int ny) {
+// does the site n = a - p lie inside or on (with a margin) one of the
+// vertex discs in the bit set `discs` (those meeting the site's row band)?
+__device__ __forceinline__ bool in_flower(const FlowerSmem &F, unsigned discs, int nx, int ny) {
     const float fnx = (float)nx, fny = (float)ny;
     const float nn = fmaf(fnx, fnx, fny * fny);
-    for (int q = 0; q < e; q++) {
+    while (discs) {
+        const int q = __ffs(discs) - 1;
+        discs &= discs - 1;
         const float px = fnx * F.wx[q], py = fny * F.wy[q];
         const float f = 2.f * (px + py) - nn;
         const float mg = 0x1p-16f * (2.f * (fabsf(px) + fabsf(py)) + nn) + 1.f;
@@ -159,9 +163,11 @@ __global__ void __launch_bounds__(32 * FL_WARPS) flower_gather_kernel(CellParams
         __syncwarp();
         // the row ranges meeting the flower: the union of the vertex discs'
         // chords over the row's band
+        unsigned discs = 0;                                // of the last row given to span
         auto span = [&](int row, int *x0, int *x1) -> int {
             const float fy0 = (float)row * (float)s, fy1 = fy0 + (float)s;
             float xlo = FLT_MAX, xhi = -FLT_MAX;
+            discs = 0;
             for (int q = 0; q < e1; q++) {
                 const float cy = (float)p.y + F.wy[q];
                 const float dv = fmaxf(0.f, fmaxf(fy0 - cy, cy - fy1));
@@ -170,6 +176,7 @@ __global__ void __launch_bounds__(32 * FL_WARPS) flower_gather_kernel(CellParams
                 const float cx = (float)p.x + F.wx[q];
                 xlo = fminf(xlo, cx - h);
                 xhi = fmaxf(xhi, cx + h);
+                discs |= 1u << q;
             }
             if (xlo > xhi) return 0;
             x0[0] = max(0, (int)floorf(fmaxf(xlo, -1.f) / (float)s));
@@ -184,8 +191,10 @@ __global__ void __launch_bounds__(32 * FL_WARPS) flower_gather_kernel(CellParams
         for (int r0 = by0; r0 <= by1; r0 += 32) {
             const int row = r0 + lane;
             int x0, x1;
-            if (row <= by1)
+            if (row <= by1) {
                 F.held[row - by0] = span(row, &x0, &x1) ? g.bs[row * g.m1 + x1 + 1] - g.bs[row * g.m1 + x0] : 0;
+                F.disc[row - by0] = (unsigned short)discs;
+            }
         }
         __syncwarp();
         int lo = prow, hi = prow - 1;                      // rows read: [lo, hi]
@@ -219,6 +228,7 @@ __global__ void __launch_bounds__(32 * FL_WARPS) flower_gather_kernel(CellParams
             __syncwarp();
             continue;
         }
+        const int rb0 = by0;                               // the pre-pass's first row (F.held, F.disc)
         by0 = lo;
         by1 = hi;
         // the listed sites lie closer than sqrt(lim2) (integer, at most rt^2)
@@ -238,7 +248,7 @@ __global__ void __launch_bounds__(32 * FL_WARPS) flower_gather_kernel(CellParams
             if (pos == i) return;
             const int ax = q.x - p.x, ay = q.y - p.y;
             const i64 dd = (i64)ax * ax + (i64)ay * ay;
-            if (dd >= lim2 || !in_flower(F, e1, ax, ay)) return;
+            if (dd >= lim2 || !in_flower(F, F.disc[q.y / s - rb0], ax, ay)) return;
             atomicAdd(&F.hist[min(31, (int)((float)dd * binscale))], 1);
         };
         scan_rows<32, 1, 2>(g, P.sxy, by0, by1, lane, FULL, span, count);
@@ -259,7 +269,7 @@ __global__ void __launch_bounds__(32 * FL_WARPS) flower_gather_kernel(CellParams
         auto list = [&](int pos, int2 q) {
             if (pos == i) return;
             const int ax = q.x - p.x, ay = q.y - p.y;
-            if ((i64)ax * ax + (i64)ay * ay >= lim2 || !in_flower(F, e1, ax, ay)) return;
+            if ((i64)ax * ax + (i64)ay * ay >= lim2 || !in_flower(F, F.disc[q.y / s - rb0], ax, ay)) return;
             const int at = atomicAdd(&F.cnt, 1);
             if (at < GMAX) {
                 G.tab[G.at(t, at)] = t1::cand_of(ax, ay);

@@ -947,12 +947,15 @@ static int launch_build(const BatchArgs &A, const vor_opts *o, void *ws, const L
         if (launch_gather_pass(P2, 2, gcount, grho2, gtab, glab, st) != cudaSuccess) return VOR_E_CUDA;
         P2.next_cell = &hdr->pass_next[1];
         if (launch_cells_pass(P2, 2, gcount, grho2, gtab, glab, st) != cudaSuccess) return VOR_E_CUDA;
-        // flower passes: the flower of the polygon an earlier pass left, its
-        // sites nearest p first, up to 124 entries; a cell its certificate
-        // does not accept leaves the new polygon for the next flower pass,
-        // and what is left after the last goes to the medium tier
+        // flower passes (batches of several sets, where small clustered sets
+        // leave many cells uncertified; a single set leaves too few for a
+        // pass that fills the GPU): the flower of the polygon an earlier
+        // pass left, its sites nearest p first, up to 124 entries; a cell its
+        // certificate does not accept leaves the new polygon for the next
+        // flower pass, and what is left after the last goes to the medium tier
         int *fin = deferred2, *fin_count = &hdr->ndeferred2;
-        for (int f = 0; f < FLOWER_PASSES; f++) {
+        const int passes = L.n_sets > 1 ? FLOWER_PASSES : 0;
+        for (int f = 0; f < passes; f++) {
             int *fout = (f & 1) ? deferred2 : deferred5;
             CellParams P3 = P2;
             P3.cell_list = fin;
@@ -970,8 +973,8 @@ static int launch_build(const BatchArgs &A, const vor_opts *o, void *ws, const L
         }
         med_list = fin;
         med_count = fin_count;
-        if (cudaMemsetAsync(&hdr->flower_passes, FLOWER_PASSES, 1, st) != cudaSuccess) return VOR_E_CUDA;
-        launched += 4 + 2 * FLOWER_PASSES;
+        if (passes && cudaMemsetAsync(&hdr->flower_passes, passes, 1, st) != cudaSuccess) return VOR_E_CUDA;
+        launched += 4 + 2 * passes;
         mark(4, st);
     } else {
         P.deferred = deferred2;
