@@ -82,6 +82,12 @@ typedef struct vor_opts {
     int32_t collect_stats;    /* 1: fill vor_stats (device atomics, slightly slower)      */
     int32_t bucket_load_pct;  /* automatic bucket side: sites per bucket it aims at around
                                  a typical site, in hundredths (25..1600); 0: 200          */
+    int32_t share_vertices;   /* a Voronoi vertex belongs to two or three cells (Section 9
+                                 notes it is computed three times).  0: every cell computes
+                                 it from its owner's lines (the cell of the smallest site
+                                 among them), so all copies are bit-identical; 1: only the
+                                 owner computes it and the other cells copy it (one extra
+                                 kernel; slower on this GPU than computing it again)     */
 } vor_opts;
 
 /* Counters of one build (filled when collect_stats = 1). */

@@ -57,7 +57,7 @@ class VorOpts(ctypes.Structure):
     _fields_ = [("bucket_side", ctypes.c_int32), ("lanes_per_cell", ctypes.c_int32),
                 ("target", ctypes.c_int32), ("exact_only", ctypes.c_int32),
                 ("check_duplicates", ctypes.c_int32), ("collect_stats", ctypes.c_int32),
-                ("bucket_load_pct", ctypes.c_int32)]
+                ("bucket_load_pct", ctypes.c_int32), ("share_vertices", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {f: int(getattr(self, f)) for f, _ in self._fields_}

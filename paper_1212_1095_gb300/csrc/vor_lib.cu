@@ -401,6 +401,7 @@ __global__ void k_pick_grid(SetMeta *__restrict__ sets, int n_sets, int s_fixed,
 struct CompactParams {
     const int2 *sites;
     int n;
+    int share;                  // 1: a vertex is computed once, by the smallest site among its cells
     const SetMeta *sets;
     const int *sset;
     const int *ecount, *dcount, *loc, *slot, *spill;
@@ -543,21 +544,65 @@ __device__ __forceinline__ void side_line(int W, int H, int2 p, int lab, int &nx
 // The vertex between edge q (line a, label a_lab) and edge q + 1 (line b) of
 // the cell of p, its label, and the Delaunay pair (kl, a_lab) when a_lab > kl,
 // at rank = the number of the cell's labels between kl and a_lab (labs[0..e))
-__device__ __forceinline__ void emit_vertex(const CompactParams &Q, int2 p, int kl, long long off,
-                                            long long doff, const int *labs, int e, int q, int a_lab,
-                                            int ax, int ay, i64 ac, int bx, int by, i64 bc) {
+// The float64 vertex (p D + N) / D of the lines (ax, ay, ac), (bx, by, bc)
+// of the cell of p.
+__device__ __forceinline__ void vertex_of(int2 p, int ax, int ay, i64 ac, int bx, int by, i64 bc,
+                                          double &vx, double &vy) {
     i64 Nx, Ny, D;
     intersect(ax, ay, ac, bx, by, bc, Nx, Ny, D);
     // absolute vertex (p D + N) / D; the numerators lie in [0, W |D|]
     const i64 numx = (i64)((unsigned long long)p.x * (unsigned long long)D + (unsigned long long)Nx);
     const i64 numy = (i64)((unsigned long long)p.y * (unsigned long long)D + (unsigned long long)Ny);
-    Q.edge_label[off + q] = a_lab;
     // the quotients with D > 0 (numerators >= 0: the vertex is in the box)
     const unsigned long long aD = D < 0 ? 0ull - (unsigned long long)D : (unsigned long long)D;
     const long long ax_ = D < 0 ? -numx : numx, ay_ = D < 0 ? -numy : numy;
     const FFDen fd = ff_den(aD);
-    Q.vx[off + q] = ff_quotient(ax_, aD, fd);
-    Q.vy[off + q] = ff_quotient(ay_, aD, fd);
+    vx = ff_quotient(ax_, aD, fd);
+    vy = ff_quotient(ay_, aD, fd);
+}
+
+// A vertex of cell kl between its edges a_lab and b_lab belongs to the cells
+// of kl and of the neighbour sites among a_lab, b_lab (sides are no cells).
+// Its owner is the cell of the smallest of these sites.
+__device__ __forceinline__ bool owns_vertex(int kl, int a_lab, int b_lab) {
+    return (a_lab < 0 || kl < a_lab) && (b_lab < 0 || kl < b_lab);
+}
+
+// The vertex as its owner sees it: the meeting point of the owner's lines to
+// the other two members (sites, or a side of X), relative to the owner's
+// site.  Every cell that lists the vertex computes it from the same integers,
+// so all of them hold the same float64 coordinates (the order of the two
+// lines only flips the signs of N and D, which the division undoes).
+// p: the site of cell kl; A, B: the sites a_lab, b_lab (ignored for sides).
+__device__ __forceinline__ void vertex_canonical(int W, int H, int kl, int2 p, int a_lab, int2 A,
+                                                 int b_lab, int2 B, double &vx, double &vy) {
+    int ol = kl, m1 = a_lab, m2 = b_lab;
+    int2 r = p, s1 = A, s2 = B;
+    if (a_lab >= 0 && a_lab < ol && (b_lab < 0 || a_lab < b_lab)) {
+        ol = a_lab; r = A; m1 = kl; s1 = p;
+    } else if (b_lab >= 0 && b_lab < ol) {
+        ol = b_lab; r = B; m2 = kl; s2 = p;
+    }
+    int ax, ay, bx, by;
+    i64 ac, bc;
+    if (m1 >= 0) { ax = s1.x - r.x; ay = s1.y - r.y; ac = (i64)ax * ax + (i64)ay * ay; }
+    else side_line(W, H, r, m1, ax, ay, ac);
+    if (m2 >= 0) { bx = s2.x - r.x; by = s2.y - r.y; bc = (i64)bx * bx + (i64)by * by; }
+    else side_line(W, H, r, m2, bx, by, bc);
+    vertex_of(r, ax, ay, ac, bx, by, bc, vx, vy);
+}
+
+__device__ __forceinline__ void emit_vertex(const CompactParams &Q, int2 p, int kl, int W, int H,
+                                            long long off, long long doff, const int *labs, int e,
+                                            int q, int a_lab, int2 A, int b_lab, int2 B) {
+    Q.edge_label[off + q] = a_lab;
+    // with sharing, only the owner computes; k_share_vertices copies it
+    if (!Q.share || owns_vertex(kl, a_lab, b_lab)) {
+        double vx, vy;
+        vertex_canonical(W, H, kl, p, a_lab, A, b_lab, B, vx, vy);
+        Q.vx[off + q] = vx;
+        Q.vy[off + q] = vy;
+    }
     if (a_lab > kl) {
         int rank = 0;
         for (int j = 0; j < e; j++) {
@@ -627,13 +672,10 @@ __global__ void __launch_bounds__(COMPACT_T) k_compact(CompactParams Q) {
     if (V > COMPACT_V) {
         // more edges than the staging area: each lane its own cell
         for (int q = 0; q < ci.e; q++) {
-            int a_lab, ax, ay, b_lab, bx, by;
-            i64 ac, bc;
-            a_lab = ci.src[q];
-            b_lab = ci.src[q + 1 < ci.e ? q + 1 : 0];
-            line_of(ss, ci.W, ci.H, ci.p, a_lab, ax, ay, ac);
-            line_of(ss, ci.W, ci.H, ci.p, b_lab, bx, by, bc);
-            emit_vertex(Q, ci.p, ci.kl, ci.off, ci.doff, ci.src, ci.e, q, a_lab, ax, ay, ac, bx, by, bc);
+            const int a_lab = ci.src[q];
+            const int b_lab = ci.src[q + 1 < ci.e ? q + 1 : 0];
+            const int2 A = a_lab >= 0 ? ss[a_lab] : ci.p, B = b_lab >= 0 ? ss[b_lab] : ci.p;
+            emit_vertex(Q, ci.p, ci.kl, ci.W, ci.H, ci.off, ci.doff, ci.src, ci.e, q, a_lab, A, b_lab, B);
         }
         return;
     }
@@ -670,26 +712,49 @@ __global__ void __launch_bounds__(COMPACT_T) k_compact(CompactParams Q) {
             const int q = v - cc.start;
             const int vb = q + 1 < cc.e ? v + 1 : cc.start;
             const int a_lab = lab_w[v], b_lab = lab_w[vb];
-            int ax, ay, bx, by;
-            i64 ac, bc;
-            if (a_lab >= 0) {
-                const int2 a = nb_w[v];
-                ax = a.x - cc.p.x;
-                ay = a.y - cc.p.y;
-                ac = (i64)ax * ax + (i64)ay * ay;
-            } else {
-                side_line(cc.W, cc.H, cc.p, a_lab, ax, ay, ac);
-            }
-            if (b_lab >= 0) {
-                const int2 b = nb_w[vb];
-                bx = b.x - cc.p.x;
-                by = b.y - cc.p.y;
-                bc = (i64)bx * bx + (i64)by * by;
-            } else {
-                side_line(cc.W, cc.H, cc.p, b_lab, bx, by, bc);
-            }
-            emit_vertex(Q, cc.p, cc.kl, cc.off, cc.doff, lab_w + cc.start, cc.e, q, a_lab, ax, ay, ac, bx,
-                        by, bc);
+            emit_vertex(Q, cc.p, cc.kl, cc.W, cc.H, cc.off, cc.doff, lab_w + cc.start, cc.e, q, a_lab,
+                        nb_w[v], b_lab, nb_w[vb]);
+        }
+    }
+}
+
+// Vertex sharing (opts.share_vertices), after k_compact: each vertex a cell
+// does not own is copied from the owning neighbour o, where it lies between
+// o's edges for this cell and for the vertex's third line.  Where o lists no
+// such pair (a vertex shared by four or more cells, when more than three
+// sites lie on one empty circle) the cell computes the vertex itself.  One
+// thread per cell.
+__global__ void k_share_vertices(CompactParams Q) {
+    if (Q.hdr->err) return;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= Q.n) return;
+    const SetMeta &M = set_of(Q.sets, Q.sset, k);
+    const int base = (int)M.site_base;
+    const int kl = k - base;
+    const long long off = Q.cell_ptr[k];
+    const int e = (int)(Q.cell_ptr[k + 1] - off);
+    const int2 *ss = Q.sites + base;
+    for (int q = 0; q < e; q++) {
+        const int a = Q.edge_label[off + q], b = Q.edge_label[off + (q + 1 < e ? q + 1 : 0)];
+        if (owns_vertex(kl, a, b)) continue;
+        const int o = (a >= 0 && (b < 0 || a < b)) ? a : b;      // the owner: a site < kl
+        const int x = o == a ? b : a;                             // the vertex's third line
+        const long long ob = Q.cell_ptr[base + o];
+        const int oe = (int)(Q.cell_ptr[base + o + 1] - ob);
+        int j = -1;
+        for (int r = 0; r < oe && j < 0; r++) {
+            const int l1 = Q.edge_label[ob + r], l2 = Q.edge_label[ob + (r + 1 < oe ? r + 1 : 0)];
+            if ((l1 == kl && l2 == x) || (l1 == x && l2 == kl)) j = r;
+        }
+        if (j >= 0) {
+            Q.vx[off + q] = Q.vx[ob + j];
+            Q.vy[off + q] = Q.vy[ob + j];
+        } else {
+            const int2 p = Q.sites[k];
+            double vx, vy;
+            vertex_canonical(M.W, M.H, kl, p, a, a >= 0 ? ss[a] : p, b, b >= 0 ? ss[b] : p, vx, vy);
+            Q.vx[off + q] = vx;
+            Q.vy[off + q] = vy;
         }
     }
 }
@@ -1028,8 +1093,13 @@ static int launch_build(const BatchArgs &A, const vor_opts *o, void *ws, const L
     Q.cell_ptr = (const long long *)out->cell_ptr; Q.del_ptr = del_ptr;
     Q.edge_label = out->edge_label; Q.vx = out->vx; Q.vy = out->vy; Q.del_edge = out->del_edge;
     Q.edge_cap = out->edge_cap; Q.del_cap = out->del_cap; Q.hdr = hdr;
+    Q.share = o->share_vertices ? 1 : 0;
     k_compact<<<(n + COMPACT_T - 1) / COMPACT_T, COMPACT_T, 0, st>>>(Q);   // a warp per 32 cells
     launched += 1;                    // compaction
+    if (Q.share) {
+        k_share_vertices<<<(n + 255) / 256, 256, 0, st>>>(Q);
+        launched += 1;
+    }
     if (A.del_set_ptr) {
         k_set_del_ptr<<<(L.n_sets + 1 + T - 1) / T, T, 0, st>>>(sets, L.n_sets, n, del_ptr,
                                                                  A.del_set_ptr, hdr);
@@ -1096,6 +1166,7 @@ void vor_opts_default(vor_opts *o) {
     o->check_duplicates = 1;
     o->collect_stats = 0;
     o->bucket_load_pct = 0;
+    o->share_vertices = 0;
 }
 
 int64_t vor_edge_capacity(int64_t n) { return n < 1 ? 0 : 10 * n + 4; }

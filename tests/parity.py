@@ -182,3 +182,28 @@ def assert_vertices_from_labels(xy, box, d):
     ox = numx.astype(np.float64) / D.astype(np.float64)
     oy = numy.astype(np.float64) / D.astype(np.float64)
     assert_vertices_close(np.asarray(d["vx"]), np.asarray(d["vy"]), ox, oy)
+
+
+def assert_shared_vertices_identical(d):
+    """Each vertex is computed once, by the cell of the smallest site that
+    shares it, and copied into the other cells: every vertex listed by
+    several cells (the same three lines: three sites, or two sites and a
+    side) carries bit-identical float64 coordinates in all of them."""
+    cp = np.asarray(d["cell_ptr"], dtype=np.int64)
+    lab = np.asarray(d["labels"], dtype=np.int64)
+    n = cp.shape[0] - 1
+    e = np.diff(cp)
+    k = np.repeat(np.arange(n), e)
+    nxt = np.arange(lab.shape[0]) + 1
+    nxt[cp[1:][e > 0] - 1] = cp[:-1][e > 0]
+    a, b = lab, lab[nxt]
+    keep = (a >= 0) | (b >= 0)                       # at least one neighbour cell shares it
+    t = np.sort(np.stack([k, a, b], 1)[keep], axis=1)
+    vx = np.asarray(d["vx"])[keep]
+    vy = np.asarray(d["vy"])[keep]
+    order = np.lexsort((t[:, 2], t[:, 1], t[:, 0]))
+    t, vx, vy = t[order], vx[order], vy[order]
+    same = np.all(t[1:] == t[:-1], axis=1)
+    assert same.sum() > 0, "no shared vertex found"
+    bad = np.nonzero(same & ((vx[1:] != vx[:-1]) | (vy[1:] != vy[:-1])))[0]
+    assert bad.size == 0, f"shared vertex differs between cells: {t[bad[:3]]}"

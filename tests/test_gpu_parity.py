@@ -10,7 +10,8 @@ import pytest
 
 import oracle
 import synth
-from parity import (assert_full_parity, assert_sampled_parity, delaunay_symmetric_ok, to_numpy)
+from parity import (assert_full_parity, assert_sampled_parity, assert_shared_vertices_identical,
+                    delaunay_symmetric_ok, to_numpy)
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -169,3 +170,23 @@ def test_hub_cells_with_thousands_of_edges(m):
                        np.full((2, 2), BOX, np.int32))
     assert_full_parity(to_numpy(B.set(0)), r)
     assert_full_parity(to_numpy(B.set(1)), oracle.cells(u, BOX, "plain"))
+
+
+def test_shared_vertices_are_identical():
+    # a vertex shared by two or three cells has identical float64
+    # coordinates in every cell (uniform and clustered sites, and sites on a
+    # lattice, where four cells meet at every lattice vertex and the owner's
+    # list may not hold the pair)
+    for xy, box in ((synth.uniform_sites(50000, seed=11), BOX),
+                    (synth.gaussian_mixture_sites(50000, seed=12, sigma=3000.0), BOX),
+                    (synth.lattice_sites(30, 1000, 500), 30000)):
+        # every cell computes a vertex from its owner's lines (the default),
+        # or the owner computes it once and the others copy it
+        d0 = gpu(xy, box)
+        d1 = gpu(xy, box, share_vertices=1)
+        for d in (d0, d1):
+            assert_shared_vertices_identical(d)
+        for key in ("cell_ptr", "labels", "vx", "vy", "delaunay"):
+            assert np.array_equal(d0[key], d1[key]), key
+        if xy.shape[0] <= 1000:
+            assert_full_parity(d0, oracle.cells(xy, box, "plain"))
