@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-batch", action="store_true",
                     help="leave the batched sets/s and latency block out of the default line")
     ap.add_argument("--batch-steps", type=int, default=5)
+    ap.add_argument("--batch-every", type=int, default=1,
+                    help="batch workload: keep every k-th set only (a small case for profiling)")
     ap.add_argument("--requests", type=int, default=2000,
                     help="serving: requests per measured stream")
     ap.add_argument("--no-gauss", action="store_true",
@@ -305,11 +307,17 @@ def run_reference(args):
 
 
 
-def _batch_inputs(dev):
+def _batch_inputs(dev, every: int = 1):
     import numpy as np
     import torch
     import synth
     xy, ptr = synth.batch_workload()
+    if every > 1:
+        sel = np.arange(0, ptr.shape[0] - 1, every)
+        parts = [xy[ptr[j]:ptr[j + 1]] for j in sel]
+        ptr = np.zeros(len(sel) + 1, np.int64)
+        ptr[1:] = np.cumsum([p.shape[0] for p in parts])
+        xy = np.ascontiguousarray(np.concatenate(parts))
     boxes = np.full((ptr.shape[0] - 1, 2), BOX, np.int32)
     return xy, ptr, boxes, torch.from_numpy(xy).to(dev)
 
@@ -334,7 +342,7 @@ def batch_measure(args, dev, steps: int, warmup: int, ws_n: int = 1) -> dict:
 
     import paper_1212_1095_gb300 as vg
 
-    xy, ptr, boxes, d_sites = _batch_inputs(dev)
+    xy, ptr, boxes, d_sites = _batch_inputs(dev, getattr(args, "batch_every", 1))
     S, N = ptr.shape[0] - 1, int(ptr[-1])
     stream = torch.cuda.current_stream()
     # autotuning on every 7th set (an odd stride, so uniform and Gaussian
@@ -516,7 +524,8 @@ def run_batch(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
         "data": "synthetic",
-        "config": {"workload": "batch_4096", "n_sets": r["n_sets"], "n_sites": r["n_sites"],
+        "config": {"workload": "batch_4096" if args.batch_every <= 1
+                   else f"batch_4096 (every {args.batch_every}th set)", "n_sets": r["n_sets"], "n_sites": r["n_sites"],
                    "sizes": "log-uniform in [16, 65536]",
                    "distribution": "even sets uniform, odd sets 64-component Gaussian mixture",
                    "box": BOX, "l2": "256 MiB buffer written between timed steps; inputs 260 MB",
