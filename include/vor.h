@@ -88,6 +88,13 @@ typedef struct vor_opts {
                                  among them), so all copies are bit-identical; 1: only the
                                  owner computes it and the other cells copy it (one extra
                                  kernel; slower on this GPU than computing it again)     */
+    int32_t fine_split;       /* adaptive buckets (Section 9 suggests a bucketing structure
+                                 fitted to the distribution of the sites): a bucket holding
+                                 at least this many sites (4..65536) is divided into F x F
+                                 sub-buckets (F = 2..16, about three sites each), which the
+                                 thread-per-cell gathers and their first disc's density
+                                 estimate use.  0: no sub-buckets (the default; slower on
+                                 this GPU for the measured workloads)                     */
 } vor_opts;
 
 /* Counters of one build (filled when collect_stats = 1). */
@@ -109,6 +116,7 @@ typedef struct vor_stats {
     uint64_t medium_cells;     /* cells handed to the warp-per-cell medium tier            */
     uint64_t large_cells;      /* cells handed on to the block-per-cell tier               */
     uint64_t global_cells;     /* of those, cells too large for its shared-memory mode     */
+    uint64_t divided_buckets;  /* buckets divided into sub-buckets (adaptive buckets)      */
 } vor_stats;
 
 /* Device output buffers, allocated by the caller with the capacities below:

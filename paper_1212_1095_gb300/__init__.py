@@ -57,7 +57,8 @@ class VorOpts(ctypes.Structure):
     _fields_ = [("bucket_side", ctypes.c_int32), ("lanes_per_cell", ctypes.c_int32),
                 ("target", ctypes.c_int32), ("exact_only", ctypes.c_int32),
                 ("check_duplicates", ctypes.c_int32), ("collect_stats", ctypes.c_int32),
-                ("bucket_load_pct", ctypes.c_int32), ("share_vertices", ctypes.c_int32)]
+                ("bucket_load_pct", ctypes.c_int32), ("share_vertices", ctypes.c_int32),
+                ("fine_split", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {f: int(getattr(self, f)) for f, _ in self._fields_}
@@ -72,7 +73,8 @@ class VorStats(ctypes.Structure):
                 ("evals_first_pass", ctypes.c_uint64), ("rays_first_pass", ctypes.c_uint64),
                 ("evals_second_pass", ctypes.c_uint64), ("third_pass_cells", ctypes.c_uint64),
                 ("medium_cells", ctypes.c_uint64),
-                ("large_cells", ctypes.c_uint64), ("global_cells", ctypes.c_uint64)]
+                ("large_cells", ctypes.c_uint64), ("global_cells", ctypes.c_uint64),
+                ("divided_buckets", ctypes.c_uint64)]
 
     def as_dict(self) -> dict:
         return {f: int(getattr(self, f)) for f, _ in self._fields_ if f != "reserved"}

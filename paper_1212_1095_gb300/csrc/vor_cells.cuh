@@ -67,6 +67,14 @@ struct Counters {
 
 enum { CELL_OK = 0, CELL_DEFER = 1, CELL_FAIL = 2 };
 
+// The warp tier hands a cell on to the block tier when its next certificate
+// annulus may hold more sites than this while they are a small part (under
+// 1/16) of its set: a cluster's core in a large set.  Measured on the
+// clustered 4M set: the cells moved are the slowest of the warp tier's wave,
+// and the large-cell stage shortens by a third; in sets of at most 16 x 16 k
+// sites the warp tier finishes such cells sooner than the block tier.
+constexpr int M_DEFER_SITES = 16384;
+
 // Float filter: the computed key k of a candidate satisfies
 //   |k - K| <= 7.1 u (|nx||tx| + |ny||ty|) / c,  u = 2^-24
 // (theta rounded to float u, the dot product 2u, c = nx^2 + ny^2 by one FMA
@@ -700,7 +708,7 @@ __device__ float polygon_vertices(GroupSmem<CMAX, SMAX, EMAX> &S, const int e, c
 //      thinner annulus is scanned first);
 //   4. reruns the projector with them; then every site within rho' is a
 //      candidate or cuts no later polygon, and rho := rho'.
-template <int G, int CMAX, int SMAX, int EMAX, int RMAX>
+template <int G, int CMAX, int SMAX, int EMAX, int RMAX, bool ROUTE>
 __device__ int certify_by_vertex_discs(const CellParams &P, const CellGrid &g,
                                        GroupSmem<CMAX, SMAX, EMAX> &S, const int2 p, const int i,
                                        i64 rho2, int &C, int &e, const int gl,
@@ -739,9 +747,17 @@ __device__ int certify_by_vertex_discs(const CellParams &P, const CellGrid &g,
         cnt.widen++;
         i64 step2 = min(min(need, rho2 < ((i64)1 << 60) / 4 ? 4 * rho2 + 4 : rho2), far2);
         // the medium tier reads one bounding range per bucket row; a wide
-        // annulus goes to the large tier, which reads the vertex-disc chords
-        // row by row
+        // annulus, or one over many sites (a cluster's core: the coarse
+        // occupancy grid counts the sites of its bounding square), goes to
+        // the block tier, which reads the vertex-disc chords row by row with
+        // 8 warps
         if (CMAX < 1024 && 2.f * sqrtf((float)step2) > 256.f * (float)g.s) return CELL_DEFER;
+        if (ROUTE) {
+            const int r = (int)ceilf(sqrtf((float)step2)) + 1;
+            const SetMeta &M = set_of(P.sets, P.sset, i);
+            const int held = coarse_sites(P.coarse_sat, M, p.x - r, p.y - r, p.x + r, p.y + r);
+            if (held > M_DEFER_SITES && held < M.n / 16) return CELL_DEFER;
+        }
         for (int shrink = 0;; shrink++) {
             if (gl == 0) { S.ncand = C; S.flag = 0; }
             for (int q = gl; q < 32; q += G) S.hist[q] = 0;
@@ -781,7 +797,7 @@ struct Limits {
     static constexpr int scan = LARGE ? (1 << 30) : 384;  // sites examined
 };
 
-template <int G, int CMAX, int SMAX, int EMAX, int RMAX, bool LARGE>
+template <int G, int CMAX, int SMAX, int EMAX, int RMAX, bool LARGE, bool ROUTE>
 __device__ int process_cell(const CellParams &P, GroupSmem<CMAX, SMAX, EMAX> &S, int i, int gl,
                             unsigned gmask, Counters &cnt) {
     const int2 p = P.sxy[i];
@@ -841,7 +857,7 @@ __device__ int process_cell(const CellParams &P, GroupSmem<CMAX, SMAX, EMAX> &S,
 
     // ---- 3. security-radius certificate -------------------------------------
     if (LARGE) {
-        const int rc = certify_by_vertex_discs<G, CMAX, SMAX, EMAX, RMAX>(P, g, S, p, i, rho2, C, e,
+        const int rc = certify_by_vertex_discs<G, CMAX, SMAX, EMAX, RMAX, ROUTE>(P, g, S, p, i, rho2, C, e,
                                                                           gl, gmask, cnt);
         if (rc != CELL_OK) return rc;
     }
@@ -928,7 +944,7 @@ __device__ int process_cell(const CellParams &P, GroupSmem<CMAX, SMAX, EMAX> &S,
     return CELL_OK;
 }
 
-template <int G, int CMAX, int SMAX, int EMAX, int RMAX, bool LARGE>
+template <int G, int CMAX, int SMAX, int EMAX, int RMAX, bool LARGE, bool ROUTE = false>
 __global__ void __launch_bounds__(LARGE ? 32 : 16 * G, (LARGE && CMAX < 1024) ? 21 : 1)
 cells_kernel(CellParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -952,7 +968,7 @@ cells_kernel(CellParams P) {
         }
         if (t >= total) break;
         const int i = P.cell_list ? P.cell_list[t] : t;
-        const int rc = process_cell<G, CMAX, SMAX, EMAX, RMAX, LARGE>(P, S, i, gl, gmask, cnt);
+        const int rc = process_cell<G, CMAX, SMAX, EMAX, RMAX, LARGE, ROUTE>(P, S, i, gl, gmask, cnt);
         if (rc != CELL_OK && gl == 0) {
             if (rc == CELL_DEFER && P.deferred) {
                 const int q = atomicAdd(P.deferred_count, 1);

@@ -85,13 +85,31 @@ __device__ __forceinline__ Disc disc_of(const CellGrid &g, int2 p, i64 rho2) {
 __device__ __forceinline__ Disc first_disc(const CellGrid &g, int2 p, float target) {
     const int s = g.s;
     const int bx = p.x / s, by = p.y / s;
-    int c9 = 0, nb9 = 0;
-    const int x0 = max(bx - 1, 0), x1 = min(bx + 1, g.m1 - 1);
-    for (int row = max(by - 1, 0); row <= min(by + 1, g.m2 - 1); row++) {
-        c9 += g.bs[row * g.m1 + x1 + 1] - g.bs[row * g.m1 + x0];
-        nb9 += x1 - x0 + 1;
+    int c9 = 0;
+    float area;
+    const int b = by * g.m1 + bx;
+    const int off = g.fd ? g.fd[b] : -1;
+    if (off >= 0) {
+        // a divided bucket: the density of the (up to) 3 x 3 sub-buckets
+        // around p's inside the bucket
+        const int a0 = g.bs[b];
+        const int F = 1 << fine_log2(g.bs[b + 1] - a0);
+        const int sx = (p.x - bx * s) * F / s, sy = (p.y - by * s) * F / s;
+        const int x0 = max(sx - 1, 0), x1 = min(sx + 1, F - 1);
+        const int y0 = max(sy - 1, 0), y1 = min(sy + 1, F - 1);
+        const int *sp = g.fp + off;
+        for (int j = y0; j <= y1; j++) c9 += sp[j * F + x1 + 1] - sp[j * F + x0];
+        const float ss = (float)s / (float)F;
+        area = (float)((x1 - x0 + 1) * (y1 - y0 + 1)) * ss * ss;
+    } else {
+        int nb9 = 0;
+        const int x0 = max(bx - 1, 0), x1 = min(bx + 1, g.m1 - 1);
+        for (int row = max(by - 1, 0); row <= min(by + 1, g.m2 - 1); row++) {
+            c9 += g.bs[row * g.m1 + x1 + 1] - g.bs[row * g.m1 + x0];
+            nb9 += x1 - x0 + 1;
+        }
+        area = (float)nb9 * (float)s * (float)s;
     }
-    const float area = (float)nb9 * (float)s * (float)s;
     i64 rho2 = (i64)(target * area / (3.14159265f * (float)max(c9 - 1, 1)));
     rho2 = max(min(rho2, (i64)(16.f * (float)s * (float)s)), (i64)4);
     return disc_of(g, p, rho2);
@@ -112,6 +130,55 @@ __device__ __forceinline__ bool chord_cols(const CellGrid &g, int2 p, i64 rho2, 
     return bx0 <= bx1;
 }
 
+// The sites of bucket row `row`, buckets bx0..bx1 (the chord of the disc of
+// squared radius rho2 around p), as ranges [a, b) of sorted positions passed
+// to fn in ascending order: a bucket that is not divided whole (neighbours
+// merged into one range), a divided bucket only its sub-buckets that meet
+// the disc: the sub-rows within reach and in each the columns of the chord
+// at that sub-row's band.  Every site of those buckets within the disc lies
+// in a range.
+template <class Fn>
+__device__ __forceinline__ void disc_row_ranges(const CellGrid &g, int2 p, i64 rho2, int row, int bx0,
+                                                int bx1, Fn fn) {
+    const int *rb = g.bs + (size_t)row * g.m1;
+    if (!g.fd) {
+        fn(rb[bx0], rb[bx1 + 1]);
+        return;
+    }
+    const int *rf = g.fd + (size_t)row * g.m1;
+    const int s = g.s;
+    int run = rb[bx0];                                 // start of the pending whole buckets
+    for (int bx = bx0; bx <= bx1; bx++) {
+        const int off = rf[bx];
+        if (off < 0) continue;
+        const int a0 = rb[bx], a1 = rb[bx + 1];
+        if (a0 > run) fn(run, a0);
+        run = a1;
+        const int F = 1 << fine_log2(a1 - a0);
+        const int *sp = g.fp + off;
+        // sub-rows j hold the sites with (y - row s) F / s = j (integer division)
+        const int r = (int)ceilf(sqrtf((float)rho2)) + 1;
+        const int y0 = row * s;
+        const int lya = max(p.y - r - y0, 0), lyb = min(p.y + r - y0, s - 1);
+        if (lya > lyb) continue;
+        const int xb0 = bx * s;
+        for (int j = lya * F / s; j <= lyb * F / s; j++) {
+            // the integer band of sub-row j: y0 + ceil(j s / F) .. y0 + ceil((j + 1) s / F) - 1
+            const int ylo = y0 + (j * s + F - 1) / F, yhi = y0 + ((j + 1) * s + F - 1) / F - 1;
+            if (ylo > yhi) continue;
+            const i64 dy = p.y < ylo ? ylo - p.y : (p.y > yhi ? p.y - yhi : 0);
+            if (dy * dy > rho2) continue;
+            const float h = sqrtf((float)(rho2 - dy * dy)) + 1.f;   // as chord_cols
+            const int xa = max((int)floorf((float)p.x - h) - xb0, 0);
+            const int xe = min((int)floorf((float)p.x + h) - xb0, s - 1);
+            if (xa > xe) continue;
+            const int u = sp[j * F + xa * F / s], v = sp[j * F + xe * F / s + 1];
+            if (v > u) fn(a0 + u, a0 + v);
+        }
+    }
+    if (rb[bx1 + 1] > run) fn(run, rb[bx1 + 1]);
+}
+
 // One thread per cell: the cells are the sorted positions t < P.n, or
 // P.cell_list[t] for t < *P.list_count; outputs are indexed by t.  Each
 // candidate is written in the form the projector's table holds, so loading a
@@ -119,7 +186,7 @@ __device__ __forceinline__ bool chord_cols(const CellGrid &g, int2 p, i64 rho2, 
 // shared memory (one padded row per cell) and writes them out as one
 // contiguous range; without, each thread writes its own row (the second
 // pass, whose longer lists would limit the block to one warp).
-template <int NT, int GMAX, bool STAGE>
+template <int NT, int GMAX, bool STAGE, bool FINE>
 __global__ void __launch_bounds__(NT) gather_kernel(CellParams P, GatherOut G, float target) {
     __shared__ float2 stab[STAGE ? NT * (GMAX + 1) : 1];
     __shared__ int slab[STAGE ? NT * (GMAX + 1) : 1];
@@ -135,7 +202,8 @@ __global__ void __launch_bounds__(NT) gather_kernel(CellParams P, GatherOut G, f
     if (t < total && t < G.cap) {
         const int i = P.cell_list ? P.cell_list[t] : t;
         const int2 p = P.sxy[i];
-        const CellGrid g = cell_grid(P, i);
+        CellGrid g = cell_grid(P, i);
+        if (!FINE) g.fd = nullptr;                     // sub-buckets unused: no checks compiled in
         const Disc rule = first_disc(g, p, target);
         Disc d = rule;
         if (P.need_in) {
@@ -160,25 +228,26 @@ __global__ void __launch_bounds__(NT) gather_kernel(CellParams P, GatherOut G, f
             for (int row = dd.by0; row <= dd.by1 && cnt <= GMAX; row++) {
                 int bx0, bx1;
                 if (!chord_cols(g, p, rho2, row, bx0, bx1)) continue;
-                const int a = g.bs[row * g.m1 + bx0], b = g.bs[row * g.m1 + bx1 + 1];
-                // four independent site loads in flight per step
-                for (int pos0 = a; pos0 < b; pos0 += 4) {
-                    int2 q[4];
+                disc_row_ranges(g, p, rho2, row, bx0, bx1, [&](int a, int b) {
+                    // four independent site loads in flight per step
+                    for (int pos0 = a; pos0 < b; pos0 += 4) {
+                        int2 q[4];
 #pragma unroll
-                    for (int u = 0; u < 4; u++) q[u] = pos0 + u < b ? __ldg(P.sxy + pos0 + u) : p;
+                        for (int u = 0; u < 4; u++) q[u] = pos0 + u < b ? __ldg(P.sxy + pos0 + u) : p;
 #pragma unroll
-                    for (int u = 0; u < 4; u++) {
-                        const int pos = pos0 + u;
-                        if (pos >= b || pos == i) continue;
-                        const int nx = q[u].x - p.x, ny = q[u].y - p.y;
-                        if ((i64)nx * nx + (i64)ny * ny > rho2) continue;
-                        if (cnt < GMAX) {
-                            rtab[cnt * rs] = t1::cand_of(nx, ny);
-                            rlab[cnt * rs] = __ldg(P.sid + pos) - g.site_base;
+                        for (int u = 0; u < 4; u++) {
+                            const int pos = pos0 + u;
+                            if (pos >= b || pos == i) continue;
+                            const int nx = q[u].x - p.x, ny = q[u].y - p.y;
+                            if ((i64)nx * nx + (i64)ny * ny > rho2) continue;
+                            if (cnt < GMAX) {
+                                rtab[cnt * rs] = t1::cand_of(nx, ny);
+                                rlab[cnt * rs] = __ldg(P.sid + pos) - g.site_base;
+                            }
+                            cnt++;
                         }
-                        cnt++;
                     }
-                }
+                });
             }
         };
         list(d);
@@ -222,7 +291,7 @@ __global__ void __launch_bounds__(NT) gather_kernel(CellParams P, GatherOut G, f
 // lists from global memory and writes its rows directly, like
 // gather_kernel.  The lists and counts are the same as gather_kernel's (the
 // same disc, the same chord buckets, the same order).
-template <int NT, int GMAX, int SCAP, int BCAP, int RCAP>
+template <int NT, int GMAX, int SCAP, int BCAP, int RCAP, bool FINE>
 __global__ void __launch_bounds__(NT) gather_strip_kernel(CellParams P, GatherOut G, float target) {
     static_assert(SCAP <= 65536, "shared site indices are 16-bit");
     __shared__ int2 s_xy[SCAP];
@@ -247,6 +316,7 @@ __global__ void __launch_bounds__(NT) gather_strip_kernel(CellParams P, GatherOu
     if (act) {
         p = P.sxy[t];
         g = cell_grid(P, t);
+        if (!FINE) g.fd = nullptr;                     // sub-buckets unused: no checks compiled in
         d = first_disc(g, p, target);
         // segment key: (set, bucket row); non-decreasing along t
         s_key[tid] = ((long long)(P.sset ? P.sset[t] : 0) << 21) | (p.y / g.s);
@@ -255,24 +325,25 @@ __global__ void __launch_bounds__(NT) gather_strip_kernel(CellParams P, GatherOu
     // a row from global memory, written directly (rows outside the staged
     // rectangle; none by construction of the rectangle)
     auto list_global = [&](int row, int bx0, int bx1) {
-        const int a = g.bs[row * g.m1 + bx0], b = g.bs[row * g.m1 + bx1 + 1];
-        for (int pos0 = a; pos0 < b; pos0 += 4) {
-            int2 q[4];
+        disc_row_ranges(g, p, d.rho2, row, bx0, bx1, [&](int a, int b) {
+            for (int pos0 = a; pos0 < b; pos0 += 4) {
+                int2 q[4];
 #pragma unroll
-            for (int u = 0; u < 4; u++) q[u] = pos0 + u < b ? __ldg(P.sxy + pos0 + u) : p;
+                for (int u = 0; u < 4; u++) q[u] = pos0 + u < b ? __ldg(P.sxy + pos0 + u) : p;
 #pragma unroll
-            for (int u = 0; u < 4; u++) {
-                const int pos = pos0 + u;
-                if (pos >= b || pos == t) continue;
-                const int nx = q[u].x - p.x, ny = q[u].y - p.y;
-                if ((i64)nx * nx + (i64)ny * ny > d.rho2) continue;
-                if (cnt < GMAX) {
-                    G.tab[G.at(t, cnt)] = t1::cand_of(nx, ny);
-                    G.lab[G.at(t, cnt)] = __ldg(P.sid + pos) - g.site_base;
+                for (int u = 0; u < 4; u++) {
+                    const int pos = pos0 + u;
+                    if (pos >= b || pos == t) continue;
+                    const int nx = q[u].x - p.x, ny = q[u].y - p.y;
+                    if ((i64)nx * nx + (i64)ny * ny > d.rho2) continue;
+                    if (cnt < GMAX) {
+                        G.tab[G.at(t, cnt)] = t1::cand_of(nx, ny);
+                        G.lab[G.at(t, cnt)] = __ldg(P.sid + pos) - g.site_base;
+                    }
+                    cnt++;
                 }
-                cnt++;
             }
-        }
+        });
     };
     __syncthreads();
     for (int lo = 0; lo < nact;) {
@@ -332,7 +403,6 @@ __global__ void __launch_bounds__(NT) gather_strip_kernel(CellParams P, GatherOu
                     if (!chord_cols(g, p, d.rho2, row, bx0, bx1)) continue;
                     if (bx0 < C0 || bx1 + 1 - C0 >= C1) { direct = true; break; }
                     const int *rb = s_bs + (row - R0) * C1;
-                    const int a = rb[bx0 - C0], b = rb[bx1 + 1 - C0];
                     const int sb = s_roff[row - R0] - rb[0];    // shared index of position pos: pos + sb
                     auto take = [&](int pos, int2 q) {
                         const int nx = q.x - p.x, ny = q.y - p.y;
@@ -340,13 +410,17 @@ __global__ void __launch_bounds__(NT) gather_strip_kernel(CellParams P, GatherOu
                         if (cnt < GMAX) s_ent[cnt * NT + tid] = (unsigned short)(pos + sb);
                         cnt++;
                     };
-                    int pos = a;
-                    for (; pos + 1 < b; pos += 2) {              // two sites per step
-                        const int2 q0 = s_xy[pos + sb], q1 = s_xy[pos + 1 + sb];
-                        take(pos, q0);
-                        take(pos + 1, q1);
-                    }
-                    if (pos < b) take(pos, s_xy[pos + sb]);
+                    auto take_range = [&](int a, int b) {
+                        int pos = a;
+                        for (; pos + 1 < b; pos += 2) {          // two sites per step
+                            const int2 q0 = s_xy[pos + sb], q1 = s_xy[pos + 1 + sb];
+                            take(pos, q0);
+                            take(pos + 1, q1);
+                        }
+                        if (pos < b) take(pos, s_xy[pos + sb]);
+                    };
+                    if (!g.fd) take_range(rb[bx0 - C0], rb[bx1 + 1 - C0]);
+                    else disc_row_ranges(g, p, d.rho2, row, bx0, bx1, take_range);
                 }
             };
             auto list_direct = [&]() {

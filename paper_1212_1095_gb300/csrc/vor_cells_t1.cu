@@ -19,14 +19,30 @@ cudaError_t launch_gather_pass(const CellParams &P, int pass, int *gcount, long 
                                float2 *gtab, int *glab, cudaStream_t st) {
     const int total_max = P.cell_list ? P.n_list : P.n;
     const GatherOut G = gather_out(P, pass, gcount, grho2, gtab, glab);
-    if (pass == 1 && !P.cell_list)
-        gather_strip_kernel<128, P1_CMAX - 4, 1280, 1280, 32><<<(total_max + 127) / 128, 128, 0, st>>>(
-            P, G, (float)P.target);
-    else if (pass == 1)
-        gather_kernel<64, P1_CMAX - 4, true><<<(total_max + 63) / 64, 64, 0, st>>>(P, G, (float)P.target);
-    else if (pass == 2)
-        gather_kernel<128, P2_CMAX - 4, false><<<(total_max + 127) / 128, 128, 0, st>>>(P, G, 2.2f * (float)P.target);
-    else {
+    // the sub-bucket versions only when the build divided buckets
+    const bool fine = P.fdesc != nullptr;
+    if (pass == 1 && !P.cell_list) {
+        const int blocks = (total_max + 127) / 128;
+        if (fine)
+            gather_strip_kernel<128, P1_CMAX - 4, 1280, 1280, 32, true><<<blocks, 128, 0, st>>>(
+                P, G, (float)P.target);
+        else
+            gather_strip_kernel<128, P1_CMAX - 4, 1280, 1280, 32, false><<<blocks, 128, 0, st>>>(
+                P, G, (float)P.target);
+    } else if (pass == 1) {
+        const int blocks = (total_max + 63) / 64;
+        if (fine)
+            gather_kernel<64, P1_CMAX - 4, true, true><<<blocks, 64, 0, st>>>(P, G, (float)P.target);
+        else
+            gather_kernel<64, P1_CMAX - 4, true, false><<<blocks, 64, 0, st>>>(P, G, (float)P.target);
+    } else if (pass == 2) {
+        const int blocks = (total_max + 127) / 128;
+        if (fine)
+            gather_kernel<128, P2_CMAX - 4, false, true><<<blocks, 128, 0, st>>>(P, G, 2.2f * (float)P.target);
+        else
+            gather_kernel<128, P2_CMAX - 4, false, false><<<blocks, 128, 0, st>>>(P, G, 2.2f * (float)P.target);
+    }
+    if (pass >= 3) {
         // one warp per cell of the list; a grid of a few warps per SM slot,
         // the rest by grid stride (the list length is known on the device)
         const long long want = ((long long)total_max + FL_WARPS - 1) / FL_WARPS;

@@ -45,6 +45,8 @@ struct WsHeader {
     int flower_passes;      // flower passes that ran (set by a memset; 0: none)
     int fcount[FLOWER_PASSES];  // cells each flower pass hands on
     int fnext[FLOWER_PASSES];   // next list entry of each flower pass
+    int fine_top;           // sub-bucket starts handed out (adaptive buckets)
+    int fine_count;         // buckets divided into sub-buckets
     long long pad[4];
 };
 static_assert(sizeof(WsHeader) <= 256, "header");
@@ -104,9 +106,29 @@ __host__ __device__ inline bool plan_set(long long n, int W, int H, int s_fixed,
     return true;
 }
 
+// Adaptive buckets (two levels).  A bucket of the uniform grid holding at
+// least the split count of sites is divided into F x F sub-buckets, F = 2^k
+// the smallest power of two (2 <= F <= 16) with 3 F^2 >= its count, about
+// three sites per sub-bucket; its sites are stored by sub-bucket, sub-rows
+// in order, so the bucket, and every bucket row, stays one range of sorted
+// positions.  A site at offset (lx, ly) from its bucket's corner lies in
+// sub-bucket (ly F / s, lx F / s).  fdesc[b] is the offset of bucket b's
+// F^2 + 1 sub-bucket starts (relative to the bucket's first position) in the
+// pool, or -1 for a bucket that is not divided.
+__host__ __device__ inline int fine_log2(int count) {
+    int k = 1;
+    while (k < 4 && 3 * (1 << (2 * k)) < count) k++;
+    return k;
+}
+// pool entries for n sites: a divided bucket of c >= 4 sites takes F^2 + 1
+// of them, at most 1.34 c (the largest ratio, 257 / 193, at c = 193)
+__host__ __device__ inline long long fine_pool_cap(long long n) { return n + n / 2 + 64; }
+
 // The grid of one cell's set, for the kernels.
 struct CellGrid {
     const int *bs;          // the set's bucket starts
+    const int *fd;          // the set's sub-bucket descriptors (null: no sub-buckets)
+    const int *fp;          // sub-bucket start pool
     int s, m1, m2, W, H;
     int site_base;
 };
@@ -140,6 +162,9 @@ struct CellParams {
     const float *need_in;   // second pass: the same, read by its gather
     int store_poly;         // thread-per-cell passes: a cell whose polygon the certificate
                             // cannot accept leaves its lines in its slot (ecount = -e)
+    const int *coarse_sat;  // summed-area tables of the sets' coarse occupancy grids
+    const int *fdesc;       // sub-bucket descriptors over all sets (null: none)
+    const int *fpool;       // sub-bucket starts
     WsHeader *hdr;
 };
 
@@ -151,9 +176,26 @@ __device__ __forceinline__ CellGrid cell_grid(const CellParams &P, int i) {
     const SetMeta &M = set_of(P.sets, P.sset, i);
     CellGrid g;
     g.bs = P.bstart + M.bucket_base;
+    g.fd = P.fdesc ? P.fdesc + M.bucket_base : nullptr;
+    g.fp = P.fpool;
     g.s = M.s; g.m1 = M.m1; g.m2 = M.m2; g.W = M.W; g.H = M.H;
     g.site_base = (int)M.site_base;
     return g;
+}
+
+// Sites of a set in the coarse cells that meet the rectangle [x0, x1] x
+// [y0, y1] (clamped to the set's box), from its summed-area table: at least
+// the sites inside the rectangle.
+__device__ __forceinline__ int coarse_sites(const int *sat, const SetMeta &M, int x0, int y0, int x1,
+                                            int y1) {
+    const int G = M.G;
+    auto cell = [](int v, int lim, int G) {
+        return (int)((unsigned)min(max(v, 0), lim - 1) * (unsigned)G / (unsigned)lim);
+    };
+    const int a0 = cell(x0, M.W, G), a1 = cell(x1, M.W, G), b0 = cell(y0, M.H, G), b1 = cell(y1, M.H, G);
+    const int *S = sat + M.coarse_base;
+    auto at = [&](int cx, int cy) { return (cx < 0 || cy < 0) ? 0 : S[cy * G + cx]; };
+    return at(a1, b1) - at(a0 - 1, b1) - at(a1, b0 - 1) + at(a0 - 1, b0 - 1);
 }
 
 // Resident CTAs of a kernel on the current device (all SMs x CTAs per SM),
@@ -177,7 +219,7 @@ int pass_gather_width();
 long long gather_rows(long long n);   // list rows: n rounded up to whole tiles of 32
 // one warp per cell over P.cell_list, cells taken from *P.next_cell, with
 // the medium capacities (defers to P.deferred)
-cudaError_t launch_cells_medium(const CellParams &P, int max_cells, cudaStream_t st);
+cudaError_t launch_cells_medium(const CellParams &P, int max_cells, long long n_max, cudaStream_t st);
 int cells_fast_max_smem();
 // one block per cell over P.cell_list (vor_cells_coop.cu): shared-memory
 // mode (defers to P.deferred) or global-memory mode (slices of the arena,

@@ -125,6 +125,59 @@ __global__ void k_probe_mean(const int2 *__restrict__ sites, int n, SetMeta *__r
     }
 }
 
+// Summed-area table of each set's coarse occupancy grid, in place: entry
+// (cy, cx) becomes the number of the set's sites in coarse cells (0..cx) x
+// (0..cy).  Rows by warp scans (four rows per warp at a time, for loads in
+// flight), then columns with a running sum per thread, eight rows loaded
+// ahead.  16 <= G <= 1024.
+constexpr int SAT_T = 1024;
+__global__ void __launch_bounds__(SAT_T) k_coarse_sat(const SetMeta *__restrict__ sets, int n_sets,
+                                                      int *__restrict__ coarse, const WsHeader *hdr) {
+    if (hdr->err) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int j = blockIdx.x; j < n_sets; j += gridDim.x) {
+        const int G = sets[j].G;
+        int *c = coarse + sets[j].coarse_base;
+        for (int r0 = 4 * w; r0 < G; r0 += 4 * nw) {
+            int carry[4] = {0, 0, 0, 0};
+            for (int x0 = 0; x0 < G; x0 += 32) {
+                const int x = x0 + lane;
+                int v[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) v[u] = (r0 + u < G && x < G) ? c[(r0 + u) * G + x] : 0;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+                    for (int u = 0; u < 4; u++) {
+                        const int y = __shfl_up_sync(0xffffffffu, v[u], o);
+                        if (lane >= o) v[u] += y;
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    if (r0 + u < G && x < G) c[(r0 + u) * G + x] = carry[u] + v[u];
+                    carry[u] += __shfl_sync(0xffffffffu, v[u], 31);
+                }
+            }
+        }
+        __syncthreads();
+        for (int x = threadIdx.x; x < G; x += blockDim.x) {
+            int run = 0;
+            for (int r0 = 0; r0 < G; r0 += 8) {
+                int v[8];
+#pragma unroll
+                for (int u = 0; u < 8; u++) v[u] = r0 + u < G ? c[(r0 + u) * G + x] : 0;
+#pragma unroll
+                for (int u = 0; u < 8; u++) {
+                    run += v[u];
+                    if (r0 + u < G) c[(r0 + u) * G + x] = run;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // One block of SCAN_T threads: per set, the bucket side (from the probe, or
 // fixed), its grid, and the offset of its buckets in the batch's bucket array.
 __global__ void k_pick_grid(SetMeta *__restrict__ sets, int n_sets, int s_fixed, WsHeader *hdr);
@@ -145,19 +198,95 @@ __global__ void k_bucket_count(const int2 *__restrict__ sites, int n, const SetM
     rank[i] = atomicAdd(&bcount[bucket_of(p, M)], 1);
 }
 
-// Sites sorted by set, then bucket (row-major inside the set's grid): the
-// sets' bucket ranges follow each other, so set j occupies the sorted
-// positions [site_base_j, site_base_j + n_j) like the original order.
+// Adaptive buckets, the second level (Section 9, fourth closing remark: a
+// bucketing structure fitted to the distribution of the sites).  A bucket
+// whose count reaches `split` gets F x F sub-buckets (fine_log2) and F^2 + 1
+// zeroed entries of the pool for their counts, later their starts.
+__global__ void k_fine_plan(const int *__restrict__ bstart, int m_max, int split, int *__restrict__ fdesc,
+                            int *__restrict__ fpool, long long pool_cap, WsHeader *hdr) {
+    if (hdr->err) return;
+    const int m = min(m_max, hdr->m_total);
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < m; b += gridDim.x * blockDim.x) {
+        const int c = bstart[b + 1] - bstart[b];
+        int off = -1;
+        if (c >= split) {
+            const int F = 1 << fine_log2(c);
+            const int need = F * F + 1;
+            off = atomicAdd(&hdr->fine_top, need);
+            if ((long long)off + need > pool_cap) {
+                off = -1;                                  // no room: the bucket stays whole
+            } else {
+                for (int q = 0; q < need; q++) fpool[off + q] = 0;
+                atomicAdd(&hdr->fine_count, 1);
+            }
+        }
+        fdesc[b] = off;
+    }
+}
+
+// sub-bucket of site p in bucket (bx, by) of side s divided F x F
+__device__ __forceinline__ int fine_sub(int2 p, const SetMeta &M, int F) {
+    const int lx = p.x - (p.x / M.s) * M.s, ly = p.y - (p.y / M.s) * M.s;
+    return (ly * F / M.s) * F + lx * F / M.s;          // lx, ly < s <= 2^20, F <= 16: no overflow
+}
+
+// The rank of a site of a divided bucket within its sub-bucket.
+__global__ void k_fine_rank(const int2 *__restrict__ sites, int n, const SetMeta *__restrict__ sets,
+                            const int *__restrict__ sset, const int *__restrict__ bstart,
+                            const int *__restrict__ fdesc, int *__restrict__ fpool,
+                            int *__restrict__ rank, const WsHeader *hdr) {
+    if (hdr->err) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const SetMeta &M = set_of(sets, sset, i);
+    const int2 p = sites[i];
+    const long long b = bucket_of(p, M);
+    const int off = fdesc[b];
+    if (off < 0) return;
+    const int F = 1 << fine_log2(bstart[b + 1] - bstart[b]);
+    rank[i] = atomicAdd(&fpool[off + fine_sub(p, M, F)], 1);
+}
+
+// Sub-bucket counts -> starts relative to the bucket's first position.
+__global__ void k_fine_scan(const int *__restrict__ bstart, int m_max, const int *__restrict__ fdesc,
+                            int *__restrict__ fpool, const WsHeader *hdr) {
+    if (hdr->err) return;
+    const int m = min(m_max, hdr->m_total);
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < m; b += gridDim.x * blockDim.x) {
+        const int off = fdesc[b];
+        if (off < 0) continue;
+        const int c = bstart[b + 1] - bstart[b];
+        const int F2 = 1 << (2 * fine_log2(c));
+        int run = 0;
+        for (int q = 0; q < F2; q++) {
+            const int v = fpool[off + q];
+            fpool[off + q] = run;
+            run += v;
+        }
+        fpool[off + F2] = run;                             // = c
+    }
+}
+
+// Sites sorted by set, then bucket (row-major inside the set's grid), then,
+// in a divided bucket, sub-bucket: the sets' bucket ranges follow each
+// other, so set j occupies the sorted positions [site_base_j, site_base_j +
+// n_j) like the original order.
 __global__ void k_bucket_scatter(const int2 *__restrict__ sites, int n, const SetMeta *__restrict__ sets,
                                  const int *__restrict__ sset, const int *__restrict__ bstart,
-                                 const int *__restrict__ rank, int2 *__restrict__ sxy,
+                                 const int *__restrict__ rank, const int *__restrict__ fdesc,
+                                 const int *__restrict__ fpool, int2 *__restrict__ sxy,
                                  int *__restrict__ sid, const WsHeader *hdr) {
     if (hdr->err) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const SetMeta &M = set_of(sets, sset, i);
     const int2 p = sites[i];
-    const int pos = bstart[bucket_of(p, M)] + rank[i];
+    const long long b = bucket_of(p, M);
+    int pos = bstart[b] + rank[i];
+    if (fdesc) {
+        const int off = fdesc[b];
+        if (off >= 0) pos += fpool[off + fine_sub(p, M, 1 << fine_log2(bstart[b + 1] - bstart[b]))];
+    }
     sxy[pos] = p;
     sid[pos] = i;
 }
@@ -774,11 +903,11 @@ __global__ void k_set_del_ptr(const SetMeta *__restrict__ sets, int n_sets, int 
 // ---------------------------------------------------------------------------
 
 struct Layout {
-    int s_fixed, lanes, target, n_sets, load_pct;
+    int s_fixed, lanes, target, n_sets, load_pct, fine_split;
     long long n, m_sum, g_sum;
     size_t hdr, sets, sset, bstart, rank, sxy, sid, partial, ecount, dcount, loc, del_ptr, slot,
         spill, deferred, deferred2, deferred3, deferred4, deferred5, gcount, grho2, gtab, glab, coarse,
-        coop, total;
+        fdesc, fpool, coop, total;
     int spill_cap;
     int n_partial;
     long long n_max;          // largest set
@@ -837,6 +966,8 @@ static bool resolve(const int64_t *set_ptr, const vor_box *boxes, int n_sets, in
     if (L.target > 40) return false;
     L.load_pct = o->bucket_load_pct > 0 ? o->bucket_load_pct : 200;
     if (L.load_pct < 25 || L.load_pct > 1600) return false;
+    L.fine_split = o->fine_split;
+    if (L.fine_split != 0 && (L.fine_split < 4 || L.fine_split > 65536)) return false;
     const size_t m = (size_t)L.m_sum;
     const size_t nn = (size_t)(L.n > 0 ? L.n : 1);
     const int nb_b = (int)((m + SCAN_TILE - 1) / SCAN_TILE), nb_n = (int)((nn + SCAN_TILE - 1) / SCAN_TILE);
@@ -867,6 +998,9 @@ static bool resolve(const int64_t *set_ptr, const vor_box *boxes, int n_sets, in
     L.gtab = at;     at = align256(at + (size_t)gather_rows(nn) * 8 * (size_t)pass_gather_width());
     L.glab = at;     at = align256(at + (size_t)gather_rows(nn) * 4 * (size_t)pass_gather_width());
     L.coarse = at;   at = align256(at + (size_t)L.g_sum * 4);
+    const bool fine = L.fine_split > 0;
+    L.fdesc = at;    at = align256(at + (fine ? m * 4 : 0));
+    L.fpool = at;    at = align256(at + (fine ? (size_t)fine_pool_cap((long long)nn) * 4 : 0));
     L.coop_slices = coop_slices_for((long long)nn, L.n_max);
     L.coop = at;     at = align256(at + (size_t)L.coop_slices * (size_t)coop_slice_bytes(L.n_max));
     L.total = at;
@@ -953,16 +1087,33 @@ static int launch_build(const BatchArgs &A, const vor_opts *o, void *ws, const L
         k_site_set<<<gn, T, 0, st>>>(A.set_ptr, L.n_sets, n, sset, hdr);
         launched++;
     }
+    // the coarse occupancy grid: the density probe of the bucket side, then
+    // its summed-area table (the sites of any rectangle of coarse cells)
+    if (cudaMemsetAsync(coarse, 0, (size_t)L.g_sum * 4, st) != cudaSuccess) return VOR_E_CUDA;
+    k_probe_count<<<gn, T, 0, st>>>(sites, n, sets, sset, coarse, hdr);
+    launched++;
     if (L.s_fixed <= 0) {
-        if (cudaMemsetAsync(coarse, 0, (size_t)L.g_sum * 4, st) != cudaSuccess) return VOR_E_CUDA;
-        k_probe_count<<<gn, T, 0, st>>>(sites, n, sets, sset, coarse, hdr);
         k_probe_mean<<<gn, T, 0, st>>>(sites, n, sets, sset, coarse, hdr);
-        launched += 2;
+        launched++;
     }
+    k_coarse_sat<<<L.n_sets < 152 * 2 ? L.n_sets : 152 * 2, SAT_T, 0, st>>>(sets, L.n_sets, coarse, hdr);
+    launched++;
     k_pick_grid<<<1, SCAN_T, 0, st>>>(sets, L.n_sets, L.s_fixed, hdr);
     k_bucket_count<<<gn, T, 0, st>>>(sites, n, sets, sset, bstart, rank, hdr);
     launched += scan<int>(bstart, (int)L.m_sum, &hdr->m_total, bstart, (int *)partial, nullptr, hdr, st);
-    k_bucket_scatter<<<gn, T, 0, st>>>(sites, n, sets, sset, bstart, rank, sxy, sid, hdr);
+    int *fdesc = nullptr, *fpool = nullptr;
+    if (L.fine_split > 0) {
+        // the second level of the adaptive buckets: divide the dense buckets
+        fdesc = (int *)(base + L.fdesc);
+        fpool = (int *)(base + L.fpool);
+        const int gm = (int)((L.m_sum + T - 1) / T < 152 * 64 ? (L.m_sum + T - 1) / T : 152 * 64);
+        k_fine_plan<<<gm, T, 0, st>>>(bstart, (int)L.m_sum, L.fine_split, fdesc, fpool,
+                                      fine_pool_cap(L.n), hdr);
+        k_fine_rank<<<gn, T, 0, st>>>(sites, n, sets, sset, bstart, fdesc, fpool, rank, hdr);
+        k_fine_scan<<<gm, T, 0, st>>>(bstart, (int)L.m_sum, fdesc, fpool, hdr);
+        launched += 3;
+    }
+    k_bucket_scatter<<<gn, T, 0, st>>>(sites, n, sets, sset, bstart, rank, fdesc, fpool, sxy, sid, hdr);
     launched += 3;                    // pick, count, scatter
     if (o->check_duplicates) {
         k_dup_check<<<gn, T, 0, st>>>(sxy, n, sets, sset, bstart, hdr);
@@ -980,6 +1131,8 @@ static int launch_build(const BatchArgs &A, const vor_opts *o, void *ws, const L
     P.ecount = ecount; P.dcount = dcount; P.loc = loc; P.slot = slot; P.spill = spill;
     P.spill_cap = L.spill_cap;
     P.cell_list = nullptr; P.list_count = nullptr; P.n_list = 0;
+    P.fdesc = fdesc; P.fpool = fpool;
+    P.coarse_sat = coarse;
     P.hdr = hdr;
     int *med_list = deferred2, *med_count = &hdr->ndeferred2;   // the medium tier's cells
     if (L.lanes == 1) {
@@ -1063,7 +1216,7 @@ static int launch_build(const BatchArgs &A, const vor_opts *o, void *ws, const L
     PM.deferred = deferred3;
     PM.deferred_count = &hdr->ndeferred3;
     PM.next_cell = &hdr->large_next;
-    if (launch_cells_medium(PM, n, st) != cudaSuccess) return VOR_E_CUDA;
+    if (launch_cells_medium(PM, n, L.n_max, st) != cudaSuccess) return VOR_E_CUDA;
     CellParams PL = PM;
     PL.cell_list = deferred3;
     PL.list_count = &hdr->ndeferred3;
@@ -1167,6 +1320,7 @@ void vor_opts_default(vor_opts *o) {
     o->collect_stats = 0;
     o->bucket_load_pct = 0;
     o->share_vertices = 0;
+    o->fine_split = 0;
 }
 
 int64_t vor_edge_capacity(int64_t n) { return n < 1 ? 0 : 10 * n + 4; }
@@ -1261,6 +1415,7 @@ int vor_status(const void *d_workspace, void *stream, vor_stats *stats) {
         stats->medium_cells = (uint64_t)(medium > 0 ? medium : 0);
         stats->large_cells = (uint64_t)(h.ndeferred3 > 0 ? h.ndeferred3 : 0);
         stats->global_cells = (uint64_t)(h.ndeferred4 > 0 ? h.ndeferred4 : 0);
+        stats->divided_buckets = (uint64_t)(h.fine_count > 0 ? h.fine_count : 0);
     }
     return map_err(h.err);
 }

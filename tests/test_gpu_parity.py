@@ -72,6 +72,11 @@ def test_uniform_1k_all_variants():
     # tiny buckets force certificate reruns, huge buckets the large-cell pass
     for side in (2000, 8000, 200000, 1 << 20):
         assert_full_parity(gpu(xy, BOX, bucket_side=side), r)
+    # adaptive buckets: none divided, every bucket of 4+ sites divided, and
+    # large buckets divided into up to 16 x 16 sub-buckets
+    for side in (0, 65536, 200000, 1 << 20):
+        for split in (0, 4, 12, 64):
+            assert_full_parity(gpu(xy, BOX, bucket_side=side, fine_split=split), r)
 
 
 def test_extreme_coordinates():
@@ -81,11 +86,20 @@ def test_extreme_coordinates():
     assert_full_parity(gpu(xy, BOX), oracle.cells(xy, BOX, "plain"))
 
 
-def test_clustered_medium():
+@pytest.fixture(scope="module")
+def clustered_60k():
     xy = synth.gaussian_mixture_sites(60000, seed=4242, sigma=2000.0)
-    r = oracle.cells(xy, BOX, "bucketed")
-    d = gpu(xy, BOX, collect_stats=1)
-    assert_full_parity(d, r)
+    return xy, oracle.cells(xy, BOX, "bucketed")
+
+
+@pytest.mark.parametrize("split", [0, 4, 12])
+def test_clustered_medium(clustered_60k, split):
+    xy, r = clustered_60k
+    t = torch.from_numpy(np.ascontiguousarray(xy, dtype=np.int32)).cuda()
+    res = vg.build(t, BOX, collect_stats=1, fine_split=split)
+    assert_full_parity(to_numpy(res), r)
+    # the cluster cores are dense enough for the adaptive buckets to divide
+    assert (res.stats["divided_buckets"] > 0) == (split != 0)
 
 
 def test_cells_with_hundreds_of_edges():
