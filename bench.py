@@ -345,7 +345,7 @@ def batch_measure(args, dev, steps: int, warmup: int, ws_n: int = 1) -> dict:
     xy, ptr, boxes, d_sites = _batch_inputs(dev, getattr(args, "batch_every", 1))
     S, N = ptr.shape[0] - 1, int(ptr[-1])
     stream = torch.cuda.current_stream()
-    # autotuning on every 7th set (an odd stride, so uniform and Gaussian
+    # autotuning on every 3rd set (an odd stride, so uniform and Gaussian
     # sets alternate in the sample); the graph replays use the winner
     fixed = args.lanes or args.target or args.bucket_side
     t0 = time.perf_counter()
@@ -354,7 +354,7 @@ def batch_measure(args, dev, steps: int, warmup: int, ws_n: int = 1) -> dict:
                                    bucket_side=args.bucket_side)
         table = []
     else:
-        d_s, sp, sb = _sub_batch(xy, ptr, np.arange(0, S, 7), dev)
+        d_s, sp, sb = _sub_batch(xy, ptr, np.arange(0, S, 3), dev)
         best, table = vg.autotune_batch(d_s, sp, sb, reps=2)
         del d_s
     tune_s = time.perf_counter() - t0
@@ -494,7 +494,7 @@ def batch_measure(args, dev, steps: int, warmup: int, ws_n: int = 1) -> dict:
         "plain": {"value": S / (plain_ms / 1000.0), "unit": "sets/s", "ms_total": plain_ms},
         "speedup_vs_plain": plain_ms / ms,
         "opts": best.as_dict(), "autotune": {
-            "sample": f"every 7th set ({(S + 6) // 7} sets)", "seconds": tune_s,
+            "sample": f"every 3rd set ({(S + 2) // 3} sets)", "seconds": tune_s,
             "candidates": [dict(c.as_dict(), ms=m) for c, m in table]},
         "graph": "one CUDA graph per batch build (captured once, replayed per step)",
         "kernels_per_build": per_build, "stages_ms": dict(zip(vg.STAGES, stages)),
@@ -784,8 +784,10 @@ def run_ours(args):
         for _ in range(1, max(1, args.e2e_callers)):
             callers.append(make_caller(vg.Workspace(n, BOX, vg.vor_opts_default(**opts), device=dev)))
 
+        e2e_steps = max(args.steps, 40)        # a timed region of ~0.1 s at least
+
         def timed(k_callers):
-            counts = [args.steps // k_callers + (1 if i < args.steps % k_callers else 0)
+            counts = [e2e_steps // k_callers + (1 if i < e2e_steps % k_callers else 0)
                       for i in range(k_callers)]
             errs = []
 
@@ -807,7 +809,7 @@ def run_ours(args):
                 for t in th:
                     t.join()
             torch.cuda.synchronize()
-            te = (time.perf_counter() - t0) / args.steps
+            te = (time.perf_counter() - t0) / e2e_steps
             if errs:
                 raise errs[0]
             return max_over_ranks(ws_n, te)
@@ -820,16 +822,21 @@ def run_ours(args):
         nd = callers[0][2].value
         d2h = 8 * (n + 1) + 20 * ne + 8 * nd
         e2e = {"value": ws_n * n / te1, "unit": "cells/s", "h2d_bytes_per_step": 8 * n,
-               "d2h_bytes_per_step": d2h, "ms_per_step": 1000.0 * te1, "callers": 1}
+               "d2h_bytes_per_step": d2h, "ms_per_step": 1000.0 * te1, "callers": 1,
+               "steps": e2e_steps}
         if len(callers) > 1:
             tec = timed(len(callers))
-            e2e = {"value": ws_n * n / tec, "unit": "cells/s", "h2d_bytes_per_step": 8 * n,
-                   "d2h_bytes_per_step": d2h, "ms_per_step": 1000.0 * tec,
-                   "callers": len(callers),
-                   "note": "host threads calling vor_build_host concurrently, each with its own "
-                           "stream, workspace and pinned buffers; every step copies its sites in "
-                           "and its results out",
-                   "one_caller": e2e}
+            multi = {"value": ws_n * n / tec, "unit": "cells/s", "h2d_bytes_per_step": 8 * n,
+                     "d2h_bytes_per_step": d2h, "ms_per_step": 1000.0 * tec,
+                     "callers": len(callers), "steps": e2e_steps,
+                     "note": "host threads calling vor_build_host concurrently, each with its "
+                             "own stream, workspace and pinned buffers; every step copies its "
+                             "sites in and its results out"}
+            # the line carries the faster of the two ways of calling, with the other beside it
+            if multi["value"] >= e2e["value"]:
+                e2e = dict(multi, one_caller=e2e)
+            else:
+                e2e = dict(e2e, concurrent_callers=multi)
         del callers
 
     b = gb = sv = None
