@@ -17,10 +17,10 @@ cudaError_t launch_cells_fast(const CellParams &P, int lanes, cudaStream_t st) {
     }
 }
 
-template <int CMAX, int SMAX, int EMAX, int RMAX, bool ROUTE>
+template <int CMAX, int SMAX, int EMAX, int RMAX, bool ROUTE, bool PAR>
 static cudaError_t launch_tier(const CellParams &P, int max_cells, cudaStream_t st) {
-    auto kern = cells_kernel<32, CMAX, SMAX, EMAX, RMAX, true, ROUTE>;
-    const int smem = (int)sizeof(GroupSmem<CMAX, SMAX, EMAX>);
+    auto kern = cells_kernel<32, CMAX, SMAX, EMAX, RMAX, true, ROUTE, PAR>;
+    const int smem = group_smem_bytes<CMAX, SMAX, EMAX>(PAR);
     int grid = 0;
     cudaError_t e = resident_grid((const void *)kern, 32, smem, grid);
     if (e != cudaSuccess) return e;
@@ -29,12 +29,16 @@ static cudaError_t launch_tier(const CellParams &P, int max_cells, cudaStream_t 
     return cudaGetLastError();
 }
 
-cudaError_t launch_cells_medium(const CellParams &P, int max_cells, long long n_max, cudaStream_t st) {
-    // the routing by site count only where a set is large enough for it
-    // (the version without it keeps the tier's registers for the rest)
-    if (n_max > 16LL * M_DEFER_SITES)
-        return launch_tier<M_CMAX, M_SMAX, M_EMAX, M_RMAX, true>(P, max_cells, st);
-    return launch_tier<M_CMAX, M_SMAX, M_EMAX, M_RMAX, false>(P, max_cells, st);
+cudaError_t launch_cells_medium(const CellParams &P, int max_cells, long long n_max, bool single,
+                                cudaStream_t st) {
+    // the routing by site count only where a set is large enough for it;
+    // the parallel subedges for a single diagram (run_projector)
+    const bool route = n_max > 16LL * M_DEFER_SITES;
+    if (single)
+        return route ? launch_tier<M_CMAX, M_SMAX, M_EMAX, M_RMAX, true, true>(P, max_cells, st)
+                     : launch_tier<M_CMAX, M_SMAX, M_EMAX, M_RMAX, false, true>(P, max_cells, st);
+    return route ? launch_tier<M_CMAX, M_SMAX, M_EMAX, M_RMAX, true, false>(P, max_cells, st)
+                 : launch_tier<M_CMAX, M_SMAX, M_EMAX, M_RMAX, false, false>(P, max_cells, st);
 }
 
 }  // namespace vor

@@ -38,6 +38,7 @@
 
 #include <cfloat>
 #include <cmath>
+#include <cstddef>
 
 #include "vor_device.cuh"
 #include "vor_internal.h"
@@ -57,7 +58,22 @@ struct __align__(16) GroupSmem {
     int ncand;                   // candidate count while appending
     int flag;
     int hist[32];                // certificate: cutters per distance bin of the annulus
+    // the parallel projector only (last, so that a launch without it can
+    // leave them out of its shared memory: group_smem_bytes)
+    long long slx[SMAX], sly[SMAX];// left corners of the stacked subedges
+    unsigned char is_edge[CMAX]; // the candidate's line carries an edge
+    int sp, nedge, perr;         // stack top, edges, error
+    int ini[6];                  // the corner rays' extreme lines
 };
+
+// Shared memory of one group: the whole struct with the parallel projector,
+// else up to its first field (one group per block only: the struct's size
+// is the stride between groups).
+template <int CMAX, int SMAX, int EMAX>
+inline int group_smem_bytes(bool par) {
+    using SM = GroupSmem<CMAX, SMAX, EMAX>;
+    return par ? (int)sizeof(SM) : (int)((offsetof(SM, slx) + 15) & ~(size_t)15);
+}
 
 struct Hit { int ccw, cw; };
 
@@ -353,6 +369,255 @@ __device__ int projector(GroupSmem<CMAX, SMAX, EMAX> &S, const int C, const int 
     if (phase < 3 || sp > 0) return -1;
     if (ne > 1 && last == first) ne--;                     // the walk closes on its first edge
     return ne;
+}
+
+// One ray shot by a group of GL lanes (the filter pass over the C candidates,
+// the reduction within the group and the decision; exact fallbacks as in
+// projector).  Returns true when u is inside the cell (vertex test only);
+// else h holds the endpoint's extreme lines.
+template <int GL, class SM>
+__device__ bool group_shoot(const SM &S, int C, int qt, i64 tx, i64 ty, int la, int lb, i64 Nx, i64 Ny,
+                            i64 D, int exact_only, int gl, unsigned gmask, Hit &h, Counters &cnt) {
+    const float fx = (float)tx, fy = (float)ty;
+    const float eth = fmaxf(fabsf(fx), fabsf(fy)) * VOR_TOL_SCALE;
+    Filt f{-FLT_MAX, -FLT_MAX, -FLT_MAX, -FLT_MAX, -1};
+    for (int c = gl; c < C; c += GL) {
+        const float4 q = S.cand[c];
+        const float den = fmaf(q.x, fx, q.y * fy);
+        const float tol = q.w * eth;
+        const float U = fmaf(den, q.z, tol);
+        const float L = fmaf(den, q.z, -tol);
+        if (U > f.u1) { f.u2 = f.u1; f.u1 = U; f.i1 = c; f.ls = L; }
+        else f.u2 = fmaxf(f.u2, U);
+        if (c != la && c != lb) f.ux = fmaxf(f.ux, U);
+    }
+    filt_reduce<GL>(f, gmask);
+    cnt.evals += C;
+    h = Hit{-1, -1};
+    if (qt == Q_UTEST) {
+        cnt.vtests++;
+        const i64 aD = D > 0 ? D : -D;
+        const float kuf = (float)(aD / 2);
+        const float klo = kuf * (1.f - 0x1p-21f), khi = kuf * (1.f + 0x1p-21f);
+        if (!exact_only && f.ux < klo) return true;
+        if (!exact_only && f.ls > f.u2 && f.ls > khi && f.i1 != la && f.i1 != lb) {
+            h = Hit{f.i1, f.i1};
+            return false;
+        }
+        cnt.exact++;
+        int viol = 0;
+        for (int c = gl; c < C && !viol; c += GL) {
+            if (c == la || c == lb) continue;
+            if (!exact_only) {
+                const float4 q = S.cand[c];
+                const float den = fmaf(q.x, fx, q.y * fy);
+                if (fmaf(den, q.z, q.w * eth) < klo) continue;
+            }
+            int nx, ny;
+            i64 cc;
+            cand_int(S, c, nx, ny, cc);
+            const i128 lhs = 2 * dot128(nx, ny, Nx, Ny) * (i128)(D > 0 ? 1 : -1);
+            if (lhs > (i128)cc * aD) viol = 1;
+        }
+        viol = group_or<GL>(viol, gmask);
+        if (!viol) return true;
+        h = exact_argmax<GL>(S, C, tx, ty, fx, fy, eth, !exact_only, f.ls, gl, gmask);
+        return false;
+    }
+    cnt.rays++;
+    if (!exact_only && f.ls > f.u2 && f.ls > 0.f) {
+        h = Hit{f.i1, f.i1};
+    } else {
+        cnt.exact++;
+        h = exact_argmax<GL>(S, C, tx, ty, fx, fy, eth, !exact_only, f.ls, gl, gmask);
+    }
+    return false;
+}
+
+// candidate a's outward normal strictly before b's counter-clockwise from
+// angle 0 (equal lines, which distinct sites cannot give, by index)
+template <class SM>
+__device__ __forceinline__ bool normal_less(const SM &S, int a, int b) {
+    int ax, ay, bx, by;
+    i64 ca, cb;
+    cand_int(S, a, ax, ay, ca);
+    cand_int(S, b, bx, by, cb);
+    if (angle_less(ax, ay, bx, by)) return true;
+    if (angle_less(bx, by, ax, ay)) return false;
+    return a < b;
+}
+
+// Algorithm 1 for one warp with NG groups of 32 / NG lanes, each group
+// taking its own subedge (Appendix 2, the parallel case: the subwedges are
+// handled independently once their corners are known).  The three corner
+// rays go to groups 0..2; then in every step each group pops one pending
+// subedge (the subwedge between its corner directions, with the lines met
+// there) and either marks the edges it finds (one line on the whole
+// subedge, or the vertex of its two lines inside the cell) or pushes the two
+// subedges of the split.  The edges, marked per candidate, are then sorted by
+// the angle of their outward normals: the counter-clockwise order of a
+// convex polygon around p, starting at the smallest angle (the canonical
+// order).  Returns the number of edges (in S.emit), or -1 when a capacity is
+// exceeded.  The counters of all groups end in lane 0's.
+template <int NG, int CMAX, int SMAX, int EMAX, int RMAX>
+__device__ int projector_par(GroupSmem<CMAX, SMAX, EMAX> &S, const int C, const int lane,
+                             const int exact_only, Counters &cnt) {
+    static_assert(NG >= 3 && 32 % NG == 0, "three corner rays, whole groups");
+    constexpr int GL = 32 / NG;
+    const unsigned FULL = 0xffffffffu;
+    const int grp = lane / GL, gl = lane % GL;
+    const unsigned gmask = (GL == 32) ? FULL : (((1u << GL) - 1u) << (grp * GL));
+    const Counters c0 = cnt;
+    for (int c = lane; c < C; c += 32) S.is_edge[c] = 0;
+    if (grp < 3) {
+        const i64 tx = grp == 0 ? 2 : (grp == 1 ? 0 : -2), ty = grp == 1 ? 1 : -1;
+        Hit h;
+        group_shoot<GL>(S, C, Q_SHOOT, tx, ty, -1, -1, 0, 0, 0, exact_only, gl, gmask, h, cnt);
+        if (gl == 0) { S.ini[2 * grp] = h.ccw; S.ini[2 * grp + 1] = h.cw; }
+    }
+    __syncwarp();
+    if (lane == 0) {
+        S.perr = (S.ini[0] < 0 || S.ini[2] < 0 || S.ini[4] < 0) ? 1 : 0;
+        // subwedges (left corner, right corner) counter-clockwise, with the
+        // counter-clockwise extreme line at the left corner, the clockwise
+        // extreme at the right one
+        const long long cx[3] = {2, 0, -2}, cy[3] = {-1, 1, -1};
+        for (int k = 0; k < 3; k++) {
+            const int kn = k == 2 ? 0 : k + 1;
+            S.slx[k] = cx[k]; S.sly[k] = cy[k];
+            S.sx[k] = cx[kn]; S.sy[k] = cy[kn];
+            S.sccw[k] = (short)S.ini[2 * k];
+            S.scw[k] = (short)S.ini[2 * kn + 1];
+        }
+        S.sp = 3;
+    }
+    __syncwarp();
+    int rays = 3;
+    for (int step = 0; !S.perr; step++) {
+        const int sp0 = S.sp;
+        if (sp0 == 0) break;
+        const int take = min(sp0, NG);
+        rays += take;
+        if (rays > RMAX + 3 * NG) { if (lane == 0) S.perr = 1; break; }
+        __syncwarp();
+        if (lane == 0) S.sp = sp0 - take;                 // the popped entries, then pushes on top
+        int k = -1;
+        i64 elx = 0, ely = 0, erx = 0, ery = 0;
+        int l1 = -1, l2 = -1;
+        if (grp < take) {
+            k = sp0 - 1 - grp;
+            elx = S.slx[k]; ely = S.sly[k]; erx = S.sx[k]; ery = S.sy[k];
+            l1 = S.sccw[k]; l2 = S.scw[k];
+        }
+        __syncwarp();
+        if (k >= 0 && l1 == l2) {                        // one line: an edge, no vertex
+            if (gl == 0) S.is_edge[l1] = 1;
+        } else if (k >= 0) {
+            int n1x, n1y, n2x, n2y;
+            i64 c1, c2, Nx, Ny, D, tx, ty;
+            cand_int(S, l1, n1x, n1y, c1);
+            cand_int(S, l2, n2x, n2y, c2);
+            intersect(n1x, n1y, c1, n2x, n2y, c2, Nx, Ny, D);
+            int qt = Q_SHOOT, la = l1, lb = l2;
+            if (D == 0) {                                  // parallel lines
+                tx = -(i64)n1y;
+                ty = (i64)n1x;
+                if (!(cross128(elx, ely, tx, ty) >= 0 && cross128(tx, ty, erx, ery) >= 0)) {
+                    tx = -tx;
+                    ty = -ty;
+                }
+                la = lb = -1;
+            } else {
+                const int sg = D > 0 ? 1 : -1;
+                const bool inw = sg * cross_sign(elx, ely, Nx, Ny) >= 0 &&
+                                 sg * cross_sign(Nx, Ny, erx, ery) >= 0;   // lambda >= 0
+                tx = sg * Nx;
+                ty = sg * Ny;
+                if (inw) {
+                    qt = Q_UTEST;                          // the ray towards u
+                } else {
+                    tx = -tx;                              // theta_3 := p - u
+                    ty = -ty;
+                    la = lb = -1;
+                }
+            }
+            Hit h;
+            const bool inside = group_shoot<GL>(S, C, qt, tx, ty, la, lb, Nx, Ny, D, exact_only, gl,
+                                                gmask, h, cnt);
+            if (gl == 0) {
+                if (inside) {                              // u is a vertex: L1, L2 carry edges
+                    S.is_edge[l1] = 1;
+                    S.is_edge[l2] = 1;
+                } else if (h.ccw < 0) {
+                    S.perr = 1;
+                } else {                                   // divide the subedge at theta_3
+                    const int at = atomicAdd(&S.sp, 2);
+                    if (at + 2 > SMAX) {
+                        S.perr = 1;
+                    } else {
+                        S.slx[at] = elx; S.sly[at] = ely; S.sx[at] = tx; S.sy[at] = ty;
+                        S.sccw[at] = (short)l1; S.scw[at] = (short)h.cw;
+                        S.slx[at + 1] = tx; S.sly[at + 1] = ty; S.sx[at + 1] = erx; S.sy[at + 1] = ery;
+                        S.sccw[at + 1] = (short)h.ccw; S.scw[at + 1] = (short)l2;
+                    }
+                }
+            }
+        }
+        __syncwarp();
+    }
+    __syncwarp();
+    // the counters of the group leaders into lane 0
+    {
+        unsigned long long d[4] = {cnt.rays - c0.rays, cnt.vtests - c0.vtests, cnt.evals - c0.evals,
+                                   cnt.exact - c0.exact};
+#pragma unroll
+        for (int z = 0; z < 4; z++) {
+            if (gl != 0) d[z] = 0;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) d[z] += __shfl_xor_sync(FULL, d[z], off);
+        }
+        cnt.rays = c0.rays + d[0];
+        cnt.vtests = c0.vtests + d[1];
+        cnt.evals = c0.evals + d[2];
+        cnt.exact = c0.exact + d[3];
+    }
+    if (S.perr) return -1;
+    // the marked edges, sorted counter-clockwise by rank
+    if (lane == 0) S.nedge = 0;
+    __syncwarp();
+    for (int c = lane; c < C; c += 32) {
+        if (S.is_edge[c]) {
+            const int at = atomicAdd(&S.nedge, 1);
+            if (at < EMAX) S.tmp[at] = (short)c;
+        }
+    }
+    __syncwarp();
+    const int ne = S.nedge;
+    if (ne > EMAX) return -1;
+    for (int q = lane; q < ne; q += 32) {
+        const int a = S.tmp[q];
+        int r = 0;
+        for (int j = 0; j < ne; j++) r += normal_less(S, S.tmp[j], a) ? 1 : 0;
+        S.emit[r] = (short)a;
+    }
+    __syncwarp();
+    return ne;
+}
+
+// The warp tier (one warp per cell) of a single diagram runs the subedges of
+// a cell on four groups of 8 lanes: few cells per warp, so a cell's latency
+// sets the tier's length (uniform 1M: 0.083 -> 0.059 ms).  A batch's warp
+// tier holds many cells per warp and is throughput-bound; there the
+// sequential walk with 32 lanes per ray is faster (4,096 sets: 35.4 vs
+// 38.0 ms), as it is for the first-pass group kernels.
+constexpr int M_PAR_GROUPS = 4;
+template <int G, int CMAX, int SMAX, int EMAX, int RMAX, bool USE_PAR>
+__device__ __forceinline__ int run_projector(GroupSmem<CMAX, SMAX, EMAX> &S, const int C, const int gl,
+                                             const unsigned gmask, const int exact_only, Counters &cnt) {
+    if constexpr (G == 32 && USE_PAR)
+        return projector_par<M_PAR_GROUPS, CMAX, SMAX, EMAX, RMAX>(S, C, gl, exact_only, cnt);
+    else
+        return projector<G, CMAX, SMAX, EMAX, RMAX>(S, C, gl, gmask, exact_only, cnt);
 }
 
 // Walk the sites of the bucket rows by0..by1 with the G lanes of a group.
@@ -708,7 +973,7 @@ __device__ float polygon_vertices(GroupSmem<CMAX, SMAX, EMAX> &S, const int e, c
 //      thinner annulus is scanned first);
 //   4. reruns the projector with them; then every site within rho' is a
 //      candidate or cuts no later polygon, and rho := rho'.
-template <int G, int CMAX, int SMAX, int EMAX, int RMAX, bool ROUTE>
+template <int G, int CMAX, int SMAX, int EMAX, int RMAX, bool ROUTE, bool PAR>
 __device__ int certify_by_vertex_discs(const CellParams &P, const CellGrid &g,
                                        GroupSmem<CMAX, SMAX, EMAX> &S, const int2 p, const int i,
                                        i64 rho2, int &C, int &e, const int gl,
@@ -782,7 +1047,7 @@ __device__ int certify_by_vertex_discs(const CellParams &P, const CellGrid &g,
             cnt.reruns++;
             cnt.cands += ncut;
             C += ncut;
-            e = projector<G, CMAX, SMAX, EMAX, RMAX>(S, C, gl, gmask, P.exact_only, cnt);
+            e = run_projector<G, CMAX, SMAX, EMAX, RMAX, PAR>(S, C, gl, gmask, P.exact_only, cnt);
             if (e < 0) return CELL_DEFER;
             if (e < 3) return CELL_FAIL;
         }
@@ -797,7 +1062,7 @@ struct Limits {
     static constexpr int scan = LARGE ? (1 << 30) : 384;  // sites examined
 };
 
-template <int G, int CMAX, int SMAX, int EMAX, int RMAX, bool LARGE, bool ROUTE>
+template <int G, int CMAX, int SMAX, int EMAX, int RMAX, bool LARGE, bool ROUTE, bool PAR>
 __device__ int process_cell(const CellParams &P, GroupSmem<CMAX, SMAX, EMAX> &S, int i, int gl,
                             unsigned gmask, Counters &cnt) {
     const int2 p = P.sxy[i];
@@ -851,13 +1116,13 @@ __device__ int process_cell(const CellParams &P, GroupSmem<CMAX, SMAX, EMAX> &S,
     group_sync<G>(gmask);
 
     // ---- 2. Algorithm 1 ----------------------------------------------------
-    int e = projector<G, CMAX, SMAX, EMAX, RMAX>(S, C, gl, gmask, P.exact_only, cnt);
+    int e = run_projector<G, CMAX, SMAX, EMAX, RMAX, LARGE && PAR>(S, C, gl, gmask, P.exact_only, cnt);
     if (e < 0) return CELL_DEFER;
     if (e < 3) return CELL_FAIL;
 
     // ---- 3. security-radius certificate -------------------------------------
     if (LARGE) {
-        const int rc = certify_by_vertex_discs<G, CMAX, SMAX, EMAX, RMAX, ROUTE>(P, g, S, p, i, rho2, C, e,
+        const int rc = certify_by_vertex_discs<G, CMAX, SMAX, EMAX, RMAX, ROUTE, PAR>(P, g, S, p, i, rho2, C, e,
                                                                           gl, gmask, cnt);
         if (rc != CELL_OK) return rc;
     }
@@ -896,7 +1161,7 @@ __device__ int process_cell(const CellParams &P, GroupSmem<CMAX, SMAX, EMAX> &S,
             cnt.reruns++;
             C += ncut;
             cnt.cands += ncut;
-            e = projector<G, CMAX, SMAX, EMAX, RMAX>(S, C, gl, gmask, P.exact_only, cnt);
+            e = run_projector<G, CMAX, SMAX, EMAX, RMAX, LARGE && PAR>(S, C, gl, gmask, P.exact_only, cnt);
             if (e < 0) return CELL_DEFER;
             if (e < 3) return CELL_FAIL;
         }
@@ -944,7 +1209,7 @@ __device__ int process_cell(const CellParams &P, GroupSmem<CMAX, SMAX, EMAX> &S,
     return CELL_OK;
 }
 
-template <int G, int CMAX, int SMAX, int EMAX, int RMAX, bool LARGE, bool ROUTE = false>
+template <int G, int CMAX, int SMAX, int EMAX, int RMAX, bool LARGE, bool ROUTE = false, bool PAR = false>
 __global__ void __launch_bounds__(LARGE ? 32 : 16 * G, (LARGE && CMAX < 1024) ? 21 : 1)
 cells_kernel(CellParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -968,7 +1233,7 @@ cells_kernel(CellParams P) {
         }
         if (t >= total) break;
         const int i = P.cell_list ? P.cell_list[t] : t;
-        const int rc = process_cell<G, CMAX, SMAX, EMAX, RMAX, LARGE, ROUTE>(P, S, i, gl, gmask, cnt);
+        const int rc = process_cell<G, CMAX, SMAX, EMAX, RMAX, LARGE, ROUTE, PAR>(P, S, i, gl, gmask, cnt);
         if (rc != CELL_OK && gl == 0) {
             if (rc == CELL_DEFER && P.deferred) {
                 const int q = atomicAdd(P.deferred_count, 1);

@@ -219,7 +219,8 @@ int pass_gather_width();
 long long gather_rows(long long n);   // list rows: n rounded up to whole tiles of 32
 // one warp per cell over P.cell_list, cells taken from *P.next_cell, with
 // the medium capacities (defers to P.deferred)
-cudaError_t launch_cells_medium(const CellParams &P, int max_cells, long long n_max, cudaStream_t st);
+cudaError_t launch_cells_medium(const CellParams &P, int max_cells, long long n_max, bool single,
+                                cudaStream_t st);
 int cells_fast_max_smem();
 // one block per cell over P.cell_list (vor_cells_coop.cu): shared-memory
 // mode (defers to P.deferred) or global-memory mode (slices of the arena,

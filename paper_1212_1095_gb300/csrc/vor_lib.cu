@@ -1216,7 +1216,7 @@ static int launch_build(const BatchArgs &A, const vor_opts *o, void *ws, const L
     PM.deferred = deferred3;
     PM.deferred_count = &hdr->ndeferred3;
     PM.next_cell = &hdr->large_next;
-    if (launch_cells_medium(PM, n, L.n_max, st) != cudaSuccess) return VOR_E_CUDA;
+    if (launch_cells_medium(PM, n, L.n_max, L.n_sets == 1, st) != cudaSuccess) return VOR_E_CUDA;
     CellParams PL = PM;
     PL.cell_list = deferred3;
     PL.list_count = &hdr->ndeferred3;
