@@ -361,7 +361,8 @@ def batch_measure(args, dev, steps: int, warmup: int, ws_n: int = 1) -> dict:
     # counters of one eager build, and the launches of one build
     Wst = vg.BatchWorkspace(ptr, boxes, vg.vor_opts_default(collect_stats=1, **{
         k: v for k, v in best.as_dict().items() if k in ("lanes_per_cell", "target",
-                                                          "bucket_side", "bucket_load_pct")}),
+                                                          "bucket_side", "bucket_load_pct",
+                                                          "block_threads")}),
         device=dev)
     Wst.launch(d_sites)
     Bst = Wst.finish()

@@ -95,6 +95,8 @@ typedef struct vor_opts {
                                  thread-per-cell gathers and their first disc's density
                                  estimate use.  0: no sub-buckets (the default; slower on
                                  this GPU for the measured workloads)                     */
+    int32_t block_threads;    /* block shape of the thread-per-cell first pass: 32, 64 or
+                                 128 threads per block; 0: 64                             */
 } vor_opts;
 
 /* Counters of one build (filled when collect_stats = 1). */
@@ -292,8 +294,10 @@ int vor_build_batch_async(const vor_site *d_sites, const int64_t *d_set_ptr,
  * candidate whose build fails gets +infinity) and the index of the fastest
  * to *best.  The arguments are those of vor_build_batch_async;
  * ws_bytes must cover vor_batch_workspace_bytes for every candidate.
- * vor_autotune_grid writes the default candidates (lanes per cell x disc
- * size x bucket load) into cand[0..max) and returns how many it wrote.
+ * vor_autotune_grid writes the default candidates (lanes per cell and block
+ * shape: one thread per cell in blocks of 32, 64 or 128 threads, or 8 lanes
+ * per cell; x disc size x bucket load: 36 in all) into cand[0..max) and
+ * returns how many it wrote.
  * Synchronous; returns VOR_OK or an argument error. */
 int32_t vor_autotune_grid(vor_opts *cand, int32_t max);
 int vor_autotune_batch(const vor_site *d_sites, const int64_t *d_set_ptr, const int64_t *h_set_ptr,

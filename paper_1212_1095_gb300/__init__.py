@@ -58,7 +58,7 @@ class VorOpts(ctypes.Structure):
                 ("target", ctypes.c_int32), ("exact_only", ctypes.c_int32),
                 ("check_duplicates", ctypes.c_int32), ("collect_stats", ctypes.c_int32),
                 ("bucket_load_pct", ctypes.c_int32), ("share_vertices", ctypes.c_int32),
-                ("fine_split", ctypes.c_int32)]
+                ("fine_split", ctypes.c_int32), ("block_threads", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {f: int(getattr(self, f)) for f, _ in self._fields_}

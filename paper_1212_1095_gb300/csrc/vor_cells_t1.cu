@@ -52,28 +52,34 @@ cudaError_t launch_gather_pass(const CellParams &P, int pass, int *gcount, long 
     return cudaGetLastError();
 }
 
-template <int CMAX>
+template <int CMAX, int NT>
 static cudaError_t launch_persist(const CellParams &P, const GatherOut &G, cudaStream_t st) {
     const int total_max = P.cell_list ? P.n_list : P.n;
-    auto kern = cells_persist_kernel<P_NT, CMAX, P_SMAX, P_EMAX, P_RMAX>;
-    const int smem = P_NT * CMAX * (int)sizeof(float2);
+    auto kern = cells_persist_kernel<NT, CMAX, P_SMAX, P_EMAX, P_RMAX>;
+    const int smem = NT * CMAX * (int)sizeof(float2);
     int resident = 0;
-    cudaError_t e = resident_grid((const void *)kern, P_NT, smem, resident);
+    cudaError_t e = resident_grid((const void *)kern, NT, smem, resident);
     if (e != cudaSuccess) return e;
-    long long want = ((long long)total_max + P_NT - 1) / P_NT;
+    long long want = ((long long)total_max + NT - 1) / NT;
     long long grid = resident;
     if (want < grid) grid = want;
     if (grid < 1) grid = 1;
-    kern<<<(unsigned)grid, P_NT, smem, st>>>(P, G);
+    kern<<<(unsigned)grid, NT, smem, st>>>(P, G);
     return cudaGetLastError();
 }
 
 cudaError_t launch_cells_pass(const CellParams &P, int pass, int *gcount, long long *grho2,
-                              float2 *gtab, int *glab, cudaStream_t st) {
+                              float2 *gtab, int *glab, int block, cudaStream_t st) {
     const GatherOut G = gather_out(P, pass, gcount, grho2, gtab, glab);
-    if (pass == 1) return launch_persist<P1_CMAX>(P, G, st);
-    if (pass == 2) return launch_persist<P2_CMAX>(P, G, st);
-    return launch_persist<P3_CMAX>(P, G, st);
+    if (pass == 1) {
+        // the block shape of the first pass (an autotuner choice): the
+        // warps' work is independent, a block shares only its launch slot
+        if (block == 32) return launch_persist<P1_CMAX, 32>(P, G, st);
+        if (block == 128) return launch_persist<P1_CMAX, 128>(P, G, st);
+        return launch_persist<P1_CMAX, P_NT>(P, G, st);
+    }
+    if (pass == 2) return launch_persist<P2_CMAX, P_NT>(P, G, st);
+    return launch_persist<P3_CMAX, P_NT>(P, G, st);
 }
 
 int pass_gather_width() { return P1_CMAX - 4; }

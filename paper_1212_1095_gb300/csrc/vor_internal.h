@@ -214,7 +214,7 @@ cudaError_t launch_cells_fast(const CellParams &P, int lanes, cudaStream_t st);
 cudaError_t launch_gather_pass(const CellParams &P, int pass, int *gcount, long long *grho2,
                                float2 *gtab, int *glab, cudaStream_t st);
 cudaError_t launch_cells_pass(const CellParams &P, int pass, int *gcount, long long *grho2,
-                              float2 *gtab, int *glab, cudaStream_t st);
+                              float2 *gtab, int *glab, int block, cudaStream_t st);
 int pass_gather_width();
 long long gather_rows(long long n);   // list rows: n rounded up to whole tiles of 32
 // one warp per cell over P.cell_list, cells taken from *P.next_cell, with

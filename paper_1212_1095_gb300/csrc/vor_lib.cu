@@ -903,7 +903,7 @@ __global__ void k_set_del_ptr(const SetMeta *__restrict__ sets, int n_sets, int 
 // ---------------------------------------------------------------------------
 
 struct Layout {
-    int s_fixed, lanes, target, n_sets, load_pct, fine_split;
+    int s_fixed, lanes, target, n_sets, load_pct, fine_split, block;
     long long n, m_sum, g_sum;
     size_t hdr, sets, sset, bstart, rank, sxy, sid, partial, ecount, dcount, loc, del_ptr, slot,
         spill, deferred, deferred2, deferred3, deferred4, deferred5, gcount, grho2, gtab, glab, coarse,
@@ -968,6 +968,8 @@ static bool resolve(const int64_t *set_ptr, const vor_box *boxes, int n_sets, in
     if (L.load_pct < 25 || L.load_pct > 1600) return false;
     L.fine_split = o->fine_split;
     if (L.fine_split != 0 && (L.fine_split < 4 || L.fine_split > 65536)) return false;
+    L.block = o->block_threads > 0 ? o->block_threads : 64;
+    if (L.block != 32 && L.block != 64 && L.block != 128) return false;
     const size_t m = (size_t)L.m_sum;
     const size_t nn = (size_t)(L.n > 0 ? L.n : 1);
     const int nb_b = (int)((m + SCAN_TILE - 1) / SCAN_TILE), nb_n = (int)((nn + SCAN_TILE - 1) / SCAN_TILE);
@@ -1151,7 +1153,7 @@ static int launch_build(const BatchArgs &A, const vor_opts *o, void *ws, const L
         mark(2, st);
         CellParams P1 = P;
         P1.next_cell = &hdr->pass_next[0];          // cells by warp generations from a counter
-        if (launch_cells_pass(P1, 1, gcount, grho2, gtab, glab, st) != cudaSuccess) return VOR_E_CUDA;
+        if (launch_cells_pass(P1, 1, gcount, grho2, gtab, glab, L.block, st) != cudaSuccess) return VOR_E_CUDA;
         mark(3, st);
         // second pass: a disc with about 2.2 times the sites
         CellParams P2 = P;
@@ -1164,7 +1166,7 @@ static int launch_build(const BatchArgs &A, const vor_opts *o, void *ws, const L
         P2.need_in = (const float *)rank;
         if (launch_gather_pass(P2, 2, gcount, grho2, gtab, glab, st) != cudaSuccess) return VOR_E_CUDA;
         P2.next_cell = &hdr->pass_next[1];
-        if (launch_cells_pass(P2, 2, gcount, grho2, gtab, glab, st) != cudaSuccess) return VOR_E_CUDA;
+        if (launch_cells_pass(P2, 2, gcount, grho2, gtab, glab, L.block, st) != cudaSuccess) return VOR_E_CUDA;
         // flower passes (batches of several sets, where small clustered sets
         // leave many cells uncertified; a single set leaves too few for a
         // pass that fills the GPU): the flower of the polygon an earlier
@@ -1185,7 +1187,7 @@ static int launch_build(const BatchArgs &A, const vor_opts *o, void *ws, const L
             P3.next_cell = nullptr;
             if (launch_gather_pass(P3, 3, gcount, grho2, gtab, glab, st) != cudaSuccess) return VOR_E_CUDA;
             P3.next_cell = &hdr->fnext[f];
-            if (launch_cells_pass(P3, 3, gcount, grho2, gtab, glab, st) != cudaSuccess) return VOR_E_CUDA;
+            if (launch_cells_pass(P3, 3, gcount, grho2, gtab, glab, L.block, st) != cudaSuccess) return VOR_E_CUDA;
             fin = fout;
             fin_count = &hdr->fcount[f];
         }
@@ -1321,6 +1323,7 @@ void vor_opts_default(vor_opts *o) {
     o->bucket_load_pct = 0;
     o->share_vertices = 0;
     o->fine_split = 0;
+    o->block_threads = 0;
 }
 
 int64_t vor_edge_capacity(int64_t n) { return n < 1 ? 0 : 10 * n + 4; }
@@ -1561,18 +1564,21 @@ int vor_vertex_quotients(const int64_t *d_num, const uint64_t *d_den, int64_t n,
 }
 
 int32_t vor_autotune_grid(vor_opts *cand, int32_t max) {
-    // lanes per cell (1: one thread per cell and the two persistent passes;
-    // 8: eight lanes per cell) x first-disc size x bucket load
-    static const int lanes[] = {1, 8};
+    // rays per warp and block shape (one thread per cell with blocks of 32,
+    // 64 or 128 threads, or eight lanes per cell in blocks of 16 groups) x
+    // first-disc size x bucket load (the grid-bucket size)
+    static const int lanes[] = {1, 1, 1, 8};
+    static const int block[] = {32, 64, 128, 0};
     static const int target[] = {16, 22, 28};
     static const int load[] = {100, 200, 400};
     int k = 0;
-    for (int a : lanes)
+    for (int a = 0; a < 4; a++)
         for (int b : target)
             for (int c : load) {
                 if (k < max && cand) {
                     vor_opts_default(&cand[k]);
-                    cand[k].lanes_per_cell = a;
+                    cand[k].lanes_per_cell = lanes[a];
+                    cand[k].block_threads = block[a];
                     cand[k].target = b;
                     cand[k].bucket_load_pct = c;
                 }

@@ -83,9 +83,11 @@ def test_batch_sizing_and_autotune_grid_on_the_host(lib):
     assert vg.vor_batch_edge_capacity(4000, 3) == 10 * 4000 + 12
     assert vg.vor_batch_delaunay_capacity(4000, 3) == 3 * 4000 + 3
     grid = vg.vor_autotune_grid()
-    assert len(grid) == 18
+    assert len(grid) == 36
     assert {g.lanes_per_cell for g in grid} == {1, 8}
+    assert {g.block_threads for g in grid if g.lanes_per_cell == 1} == {32, 64, 128}
     assert {g.bucket_load_pct for g in grid} == {100, 200, 400}
+    assert vg.vor_batch_workspace_bytes(ptr, boxes, vg.vor_opts_default(block_threads=96)) == -1
     for g in grid:
         assert vg.vor_batch_workspace_bytes(ptr, boxes, g) > 0
     assert vg.vor_kernel_launches() >= 0

@@ -69,6 +69,8 @@ def test_uniform_1k_all_variants():
         for target in (6, 20, 40):
             assert_full_parity(gpu(xy, BOX, lanes_per_cell=lanes, target=target), r)
     assert_full_parity(gpu(xy, BOX, exact_only=1), r)
+    for block in (32, 128):                            # block shapes of the first pass
+        assert_full_parity(gpu(xy, BOX, block_threads=block), r)
     # tiny buckets force certificate reruns, huge buckets the large-cell pass
     for side in (2000, 8000, 200000, 1 << 20):
         assert_full_parity(gpu(xy, BOX, bucket_side=side), r)
