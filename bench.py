@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--bucket-side", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--e2e-callers", type=int, default=2,
+    ap.add_argument("--e2e-callers", type=int, default=3,
                     help="host threads for the end-to-end measurement of single builds")
     ap.add_argument("--no-batch", action="store_true",
                     help="leave the batched sets/s and latency block out of the default line")
@@ -407,36 +407,76 @@ def batch_measure(args, dev, steps: int, warmup: int, ws_n: int = 1) -> dict:
     ms = statistics.mean(step_ms)
     ms_max = max_over_ranks(ws_n, ms)
 
-    # end to end: pinned host sites -> device, graph replay, results -> pinned host
+    # end to end: pinned host sites -> device, graph replay, results -> pinned
+    # host, every step.  Two batches in flight (two workspaces, each with its
+    # own input, outputs, pinned host buffers and graph): a batch's copies
+    # run on copy streams while the other batch builds; a slot is reused once
+    # its results are on the host.
     e2e = None
     if not args.no_e2e:
         h_sites = torch.from_numpy(xy).pin_memory()
-        h_cp = torch.empty(N + 1, dtype=torch.int64).pin_memory()
-        h_lab = torch.empty(n_edges, dtype=torch.int32).pin_memory()
-        h_vx = torch.empty(n_edges, dtype=torch.float64).pin_memory()
-        h_vy = torch.empty(n_edges, dtype=torch.float64).pin_memory()
-        h_dl = torch.empty((n_del, 2), dtype=torch.int32).pin_memory()
-        h_dsp = torch.empty(S + 1, dtype=torch.int64).pin_memory()
+        d2h = 8 * (N + 1) + 20 * n_edges + 8 * n_del + 8 * (S + 1)
 
-        def e2e_step():
-            d_sites.copy_(h_sites, non_blocking=True)
-            g.replay()
-            h_cp.copy_(W.cell_ptr, non_blocking=True)
-            h_lab.copy_(W.labels[:n_edges], non_blocking=True)
-            h_vx.copy_(W.vx[:n_edges], non_blocking=True)
-            h_vy.copy_(W.vy[:n_edges], non_blocking=True)
-            h_dl.copy_(W.del_edge[:n_del], non_blocking=True)
-            h_dsp.copy_(W.del_set_ptr, non_blocking=True)
-            stream.synchronize()
+        def host_bufs():
+            return (torch.empty(N + 1, dtype=torch.int64).pin_memory(),
+                    torch.empty(n_edges, dtype=torch.int32).pin_memory(),
+                    torch.empty(n_edges, dtype=torch.float64).pin_memory(),
+                    torch.empty(n_edges, dtype=torch.float64).pin_memory(),
+                    torch.empty((n_del, 2), dtype=torch.int32).pin_memory(),
+                    torch.empty(S + 1, dtype=torch.int64).pin_memory())
 
-        e2e_step()
+        W1 = vg.BatchWorkspace(ptr, boxes, best, device=dev)
+        d_sites1 = d_sites.clone()
+        W1.launch(d_sites1)
+        W1.finish()
+        g1 = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g1):
+            W1.launch(d_sites1)
+        slots = [(W, d_sites, g, host_bufs()), (W1, d_sites1, g1, host_bufs())]
+        s_in, s_out = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+        ev_in = [torch.cuda.Event() for _ in range(2)]
+        ev_built = [torch.cuda.Event() for _ in range(2)]
+        ev_free = [torch.cuda.Event() for _ in range(2)]
+        for e in ev_free:
+            e.record(stream)
+
+        def e2e_step(k):
+            Wk, dk, gk, hb = slots[k % 2]
+            b = k % 2
+            s_in.wait_event(ev_free[b])                   # the slot's last results are out
+            with torch.cuda.stream(s_in):
+                dk.copy_(h_sites, non_blocking=True)
+                ev_in[b].record(s_in)
+            stream.wait_event(ev_in[b])
+            gk.replay()
+            ev_built[b].record(stream)
+            s_out.wait_event(ev_built[b])
+            with torch.cuda.stream(s_out):
+                hb[0].copy_(Wk.cell_ptr, non_blocking=True)
+                hb[1].copy_(Wk.labels[:n_edges], non_blocking=True)
+                hb[2].copy_(Wk.vx[:n_edges], non_blocking=True)
+                hb[3].copy_(Wk.vy[:n_edges], non_blocking=True)
+                hb[4].copy_(Wk.del_edge[:n_del], non_blocking=True)
+                hb[5].copy_(Wk.del_set_ptr, non_blocking=True)
+                ev_free[b].record(s_out)
+
+        for k in range(2):
+            e2e_step(k)
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for _ in range(steps):
-            e2e_step()
+        for k in range(steps):
+            e2e_step(k)
+        torch.cuda.synchronize()
         te = max_over_ranks(ws_n, (time.perf_counter() - t0) / steps)
+        # the results of the last two steps equal those of the graph replays
+        ok = all(torch.equal(slots[j][3][1], slots[j][0].labels[:n_edges].cpu()) for j in range(2))
+        if not ok:
+            raise RuntimeError("end-to-end results differ between the two slots")
         e2e = {"value": ws_n * S / te, "unit": "sets/s", "h2d_bytes_per_step": 8 * N,
-               "d2h_bytes_per_step": 8 * (N + 1) + 20 * n_edges + 8 * n_del + 8 * (S + 1),
-               "ms_per_step": 1000.0 * te}
+               "d2h_bytes_per_step": d2h, "ms_per_step": 1000.0 * te,
+               "note": "two batches in flight: a batch's host<->device copies overlap the "
+                       "other batch's build"}
+        del slots, W1, g1, d_sites1
     del g, W
     torch.cuda.empty_cache()
 
@@ -825,19 +865,21 @@ def run_ours(args):
         e2e = {"value": ws_n * n / te1, "unit": "cells/s", "h2d_bytes_per_step": 8 * n,
                "d2h_bytes_per_step": d2h, "ms_per_step": 1000.0 * te1, "callers": 1,
                "steps": e2e_steps}
-        if len(callers) > 1:
-            tec = timed(len(callers))
-            multi = {"value": ws_n * n / tec, "unit": "cells/s", "h2d_bytes_per_step": 8 * n,
-                     "d2h_bytes_per_step": d2h, "ms_per_step": 1000.0 * tec,
-                     "callers": len(callers), "steps": e2e_steps,
-                     "note": "host threads calling vor_build_host concurrently, each with its "
-                             "own stream, workspace and pinned buffers; every step copies its "
-                             "sites in and its results out"}
-            # the line carries the faster of the two ways of calling, with the other beside it
-            if multi["value"] >= e2e["value"]:
-                e2e = dict(multi, one_caller=e2e)
-            else:
-                e2e = dict(e2e, concurrent_callers=multi)
+        # every count of concurrent callers up to --e2e-callers; the line
+        # carries the fastest, with the others beside it
+        others = []
+        for k in range(2, len(callers) + 1):
+            tec = timed(k)
+            others.append({"value": ws_n * n / tec, "unit": "cells/s", "h2d_bytes_per_step": 8 * n,
+                           "d2h_bytes_per_step": d2h, "ms_per_step": 1000.0 * tec,
+                           "callers": k, "steps": e2e_steps,
+                           "note": "host threads calling vor_build_host concurrently, each with "
+                                   "its own stream, workspace and pinned buffers; every step "
+                                   "copies its sites in and its results out"})
+        allv = [e2e] + others
+        best_e = max(allv, key=lambda r: r["value"])
+        e2e = dict(best_e, other_callers=[{k: r[k] for k in ("callers", "value", "ms_per_step")}
+                                          for r in allv if r is not best_e])
         del callers
 
     b = gb = sv = None
