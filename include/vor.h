@@ -76,12 +76,12 @@ typedef struct vor_opts {
     int32_t bucket_side;      /* bucket side s in units of X (Method A.5); 0: automatic     */
     int32_t lanes_per_cell;   /* lanes cooperating on one cell: 1,2,4,8,16,32; 0: automatic */
     int32_t target;           /* sites wanted in the first candidate disc around a site
-                                 (its radius follows the local bucket density); 0: automatic */
+                                 (its radius follows the local bucket density); 0: 24      */
     int32_t exact_only;       /* 1: skip the float filter, decide every ray exactly      */
     int32_t check_duplicates; /* 1: reject equal sites (VOR_E_DUPLICATE)                  */
     int32_t collect_stats;    /* 1: fill vor_stats (device atomics, slightly slower)      */
     int32_t bucket_load_pct;  /* automatic bucket side: sites per bucket it aims at around
-                                 a typical site, in hundredths (25..1600); 0: 200          */
+                                 a typical site, in hundredths (25..1600); 0: 600          */
     int32_t share_vertices;   /* a Voronoi vertex belongs to two or three cells (Section 9
                                  notes it is computed three times).  0: every cell computes
                                  it from its owner's lines (the cell of the smallest site

@@ -86,7 +86,7 @@ def test_batch_sizing_and_autotune_grid_on_the_host(lib):
     assert len(grid) == 36
     assert {g.lanes_per_cell for g in grid} == {1, 8}
     assert {g.block_threads for g in grid if g.lanes_per_cell == 1} == {32, 64, 128}
-    assert {g.bucket_load_pct for g in grid} == {100, 200, 400}
+    assert {g.bucket_load_pct for g in grid} == {200, 400, 600}
     assert vg.vor_batch_workspace_bytes(ptr, boxes, vg.vor_opts_default(block_threads=96)) == -1
     for g in grid:
         assert vg.vor_batch_workspace_bytes(ptr, boxes, g) > 0
