@@ -87,9 +87,10 @@ enum { CELL_OK = 0, CELL_DEFER = 1, CELL_FAIL = 2 };
 // annulus may hold more sites than this while they are a small part (under
 // 1/16) of its set: a cluster's core in a large set.  Measured on the
 // clustered 4M set: the cells moved are the slowest of the warp tier's wave,
-// and the large-cell stage shortens by a third; in sets of at most 16 x 16 k
-// sites the warp tier finishes such cells sooner than the block tier.
-constexpr int M_DEFER_SITES = 16384;
+// and the large-cell stage shortens by a third (thresholds of 4 k to 32 k
+// sites tried, 8 k the best); in small sets the warp tier finishes such
+// cells sooner than the block tier.
+constexpr int M_DEFER_SITES = 8192;
 
 // Float filter: the computed key k of a candidate satisfies
 //   |k - K| <= 7.1 u (|nx||tx| + |ny||ty|) / c,  u = 2^-24
