@@ -206,7 +206,8 @@ int vor_build_host(const vor_site *h_sites, int64_t n, vor_box box, const vor_op
  * > 1, ms[2] is the multi-lane pass and ms[1], ms[3] are zero.  Returns the
  * number of values written (<= max_stages) or a negative VOR_E_* code.  One
  * process-wide set of events on the current device: meant for benchmarking
- * one build at a time. */
+ * one build at a time.  A build captured into a CUDA graph while timing is
+ * enabled records the events at every replay (external event records). */
 int vor_stage_timing(int enable);
 int vor_stage_ms(float *ms, int max_stages);
 

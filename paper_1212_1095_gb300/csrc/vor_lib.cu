@@ -1019,7 +1019,14 @@ static bool g_ev_made = false;
 static bool g_ev_recorded = false;
 
 static void mark(int i, cudaStream_t st) {
-    if (g_timing) cudaEventRecord(g_ev[i], st);
+    if (!g_timing) return;
+    // inside a stream capture the events become record nodes of the graph
+    // (external records), so that every replay records them
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+        cudaEventRecordWithFlags(g_ev[i], st, cudaEventRecordExternal);
+    else
+        cudaEventRecord(g_ev[i], st);
 }
 
 // kernels launched by this library in this process (vor_kernel_launches)
