@@ -130,6 +130,14 @@ def test_errors_are_reported():
     with pytest.raises(vg.VorError) as e:
         gpu(np.array([[5, 5]]), (1 << 20) + 1)
     assert e.value.code in (-1, -4)
+    # one equal pair among 1,000 sites: found by the first pass's gather
+    # (one lane per cell) and by the per-bucket comparison (8 lanes)
+    xy = synth.workload("uniform_1k").copy()
+    xy[777] = xy[123]
+    for lanes in (1, 8):
+        with pytest.raises(vg.VorError) as e:
+            gpu(xy, BOX, lanes_per_cell=lanes)
+        assert e.value.code == -3
     # the context stays usable after device-detected errors
     d = gpu(np.array([[30, 40], [60, 20]]), 100)
     assert d["cell_ptr"][-1] > 0
