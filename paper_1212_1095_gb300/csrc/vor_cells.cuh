@@ -31,9 +31,15 @@
 //  4. Output.  The edge labels are rotated to start at the smallest normal
 //     angle and written to a fixed slot per cell (or a spill area).
 //
-// The first pass (small capacities, bounded certificate work) defers the
-// rare cells that exceed its limits; the same code with large capacities and
-// one warp per cell completes them.
+// Two uses of this code.  With several lanes per cell (lanes_per_cell > 1)
+// it is the first pass over all cells (small capacities, bounded
+// certificate work), deferring the rare cells that exceed its limits.  With
+// one warp per cell and larger capacities it is the warp tier: it takes the
+// cells the thread-per-cell passes leave, certifies them with the vertex
+// discs of the polygon (flower) over growing annuli, and hands the cells
+// that exceed it, or whose next annulus lies over a cluster's core, to the
+// block tier (vor_cells_coop.cuh).  For a single diagram the warp tier runs
+// a cell's subedges on four groups of 8 lanes (projector_par).
 #pragma once
 
 #include <cfloat>
