@@ -4,16 +4,21 @@
 // batch of one set).  Pipeline (all on one stream, no host synchronisation):
 //   K0  plan           per set: box, sizes of its grids, offsets (one block)
 //       site_set       per site: its set (batches only)
-//   K1  probe          per set: site density on a coarse grid
+//   K1  probe          per set: site counts on a coarse occupancy grid and
+//                      the density a typical site sees
+//       coarse_sat     the coarse grid's summed-area table
 //       pick_grid      per set: bucket side s (Method A.5) and bucket offsets
 //       bucket_count   validate sites (interior of X, Section 2), count sites
 //                      per bucket, record each site's rank inside its bucket
 //       scan           bucket counts -> bucket start offsets
-//       bucket_scatter sites sorted by set, then bucket, with their index
+//       fine_*         optional sub-buckets of the dense buckets
+//       bucket_scatter sites sorted by set, then bucket (and sub-bucket),
+//                      with their index
 //       dup_check      equal sites share a bucket: compare within buckets
 //   K2  cells          the projector per cell (vor_cells*.cu): two
-//                      thread-per-cell passes, then the large-cell pass over
-//                      the cells they deferred
+//                      thread-per-cell passes, flower passes (batches), the
+//                      warp tier and the block tier over the cells each
+//                      earlier stage deferred
 //       scan x2        e_k -> cell_ptr, Delaunay counts -> offsets
 //   K3  compact        CSR edge labels, float64 vertices (Section 5) and the
 //                      Delaunay pairs (Section 6), labels local to the set
