@@ -484,6 +484,54 @@ def batch_measure(args, dev, steps: int, warmup: int, ws_n: int = 1) -> dict:
     del g, W
     torch.cuda.empty_cache()
 
+    # per-set latency in waves: the sets in order of size, in WAVES batches
+    # of equal set counts (one graph each, with the tuned options), replayed
+    # back to back; a set completes with its wave, so small sets no longer
+    # wait for the large ones
+    WAVES = 8
+    sizes_all = np.diff(ptr)
+    order = np.argsort(sizes_all, kind="stable")
+    chunks = [c for c in np.array_split(order, WAVES) if len(c)]
+    wave_objs = []
+    for c in chunks:
+        d_w, sp_w, bx_w = _sub_batch(xy, ptr, c, dev)
+        Ww = vg.BatchWorkspace(sp_w, bx_w, best, device=dev)
+        Ww.launch(d_w)
+        Ww.finish()
+        gw = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gw):
+            Ww.launch(d_w)
+        wave_objs.append((d_w, Ww, gw, len(c)))
+    ev_w = [torch.cuda.Event(enable_timing=True) for _ in wave_objs]
+    for _, _, gw, _ in wave_objs:
+        gw.replay()
+    torch.cuda.synchronize()
+    wave_ms, set_lat = [], []
+    for _ in range(steps):
+        flush.fill_(1)
+        e0.record(stream)
+        for j, (_, _, gw, _) in enumerate(wave_objs):
+            gw.replay()
+            ev_w[j].record(stream)
+        ev_w[-1].synchronize()
+        done = [e0.elapsed_time(e) for e in ev_w]
+        wave_ms.append(done[-1])
+        for j, (_, _, _, cnt) in enumerate(wave_objs):
+            set_lat.extend([done[j]] * cnt)
+    for _, Ww, _, _ in wave_objs:
+        rc_w, _ = vg.vor_status(Ww.ws_ptr, stream.cuda_stream)
+        if rc_w != 0:
+            raise vg.VorError(rc_w, "batch waves")
+    waves_total = statistics.mean(wave_ms)
+    waves = {"waves": len(wave_objs), "order": "sets by size, equal set counts per wave",
+             "ms_per_step": waves_total, "value": ws_n * S / (waves_total / 1000.0),
+             "unit": "sets/s", "latency_ms": {"p50": float(np.percentile(set_lat, 50)),
+                                              "p99": float(np.percentile(set_lat, 99))},
+             "note": "one graph per wave, replayed back to back on one stream; a set's latency "
+                     "is the time from the first wave's start to its wave's completion"}
+    del wave_objs
+    torch.cuda.empty_cache()
+
     # plain: each set built by its own launch sequence, one after another on
     # the stream; a set's latency is the time from the first launch to its
     # completion
@@ -532,12 +580,14 @@ def batch_measure(args, dev, steps: int, warmup: int, ws_n: int = 1) -> dict:
         "cells_per_s": ws_n * N / (ms_max / 1000.0),
         "latency_ms": {"batched": {"p50": ms, "p99": ms,
                                    "note": "every set of a batch completes with the batch"},
+                       "waves": waves["latency_ms"],
                        "plain": {"p50": float(np.percentile(lat, 50)),
                                  "p99": float(np.percentile(lat, 99)),
                                  "note": "sets launched back to back on one stream; latency "
                                          "from the first launch to the set's completion"}},
         "plain": {"value": S / (plain_ms / 1000.0), "unit": "sets/s", "ms_total": plain_ms},
         "speedup_vs_plain": plain_ms / ms,
+        "waves": waves,
         "opts": best.as_dict(), "autotune": {
             "sample": f"every 3rd set ({(S + 2) // 3} sets)", "seconds": tune_s,
             "candidates": [dict(c.as_dict(), ms=m) for c, m in table]},
@@ -576,7 +626,7 @@ def run_batch(args):
                    "box": BOX, "l2": "256 MiB buffer written between timed steps; inputs 260 MB",
                    "graph": r["graph"], "opts": r["opts"],
                    "parallelism": f"replicas x{ws_n}" if ws_n > 1 else "1 GPU"},
-        "latency_ms": r["latency_ms"], "plain": r["plain"],
+        "latency_ms": r["latency_ms"], "plain": r["plain"], "waves": r["waves"],
         "speedup_vs_plain": r["speedup_vs_plain"], "autotune": r["autotune"],
         "cells_per_s": r["cells_per_s"], "stages_ms": r["stages_ms"], "stats": st,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TOP/s",
@@ -946,7 +996,7 @@ def run_ours(args):
     if b is not None:
         line["batched"] = {k: b[k] for k in ("value", "unit", "ms_per_step", "n_sets", "n_sites",
                                             "latency_ms", "plain", "speedup_vs_plain", "opts",
-                                            "graph", "stages_ms", "e2e")}
+                                            "graph", "stages_ms", "e2e", "waves")}
     if gb is not None:
         line["gauss_4m"] = gb
     if sv is not None:
