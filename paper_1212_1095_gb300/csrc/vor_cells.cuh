@@ -1106,6 +1106,33 @@ __device__ int process_cell(const CellParams &P, GroupSmem<CMAX, SMAX, EMAX> &S,
         rho2 /= 4;                                     // too dense: a smaller disc
     }
     int C = S.ncand;
+    if (LARGE && P.seed_poly) {
+        // An earlier pass left the polygon its certificate could not accept
+        // (ecount = -e, its lines in the slot).  Its sites outside the disc
+        // join the candidates: extra candidates never change the cell, and
+        // these lie near its final edges, so the first polygon is close to
+        // the cell and the certificate's annuli find few cutters to rerun
+        // the projector with.
+        const int e1 = -P.ecount[k];
+        if (e1 >= 3 && e1 <= SLOT_CAP) {
+            const int nset = set_of(P.sets, P.sset, i).n;
+            for (int q = gl; q < e1; q += G) {
+                const int lab = P.slot[(size_t)k * SLOT_CAP + q];
+                if (lab < 0 || lab >= nset || lab == kl) continue;
+                const int2 a = __ldg(P.sites + g.site_base + lab);
+                const int nx = a.x - p.x, ny = a.y - p.y;
+                if ((i64)nx * nx + (i64)ny * ny <= rho2) continue;   // the disc listed it
+                const int at = atomicAdd(&S.ncand, 1);
+                if (at < CMAX - 4) {
+                    const float fnx = (float)nx, fny = (float)ny, rc = 1.f / fmaf(fnx, fnx, fny * fny);
+                    S.cand[at] = make_float4(fnx, fny, rc, (float)(abs(nx) + abs(ny)) * rc);
+                    S.lab[at] = lab;
+                }
+            }
+            group_sync<G>(gmask);
+            C = min(S.ncand, CMAX - 4);
+        }
+    }
     if (gl == 0) {
         const int sx[4] = {0, g.W - p.x, 0, -p.x};
         const int sy[4] = {-p.y, 0, g.H - p.y, 0};

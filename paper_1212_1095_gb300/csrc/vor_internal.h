@@ -162,6 +162,7 @@ struct CellParams {
     const float *need_in;   // second pass: the same, read by its gather
     int store_poly;         // thread-per-cell passes: a cell whose polygon the certificate
                             // cannot accept leaves its lines in its slot (ecount = -e)
+    int seed_poly;          // warp tier: such a polygon's sites join the first candidates
     const int *coarse_sat;  // summed-area tables of the sets' coarse occupancy grids
     const int *fdesc;       // sub-bucket descriptors over all sets (null: none)
     const int *fpool;       // sub-bucket starts

@@ -1226,6 +1226,7 @@ static int launch_build(const BatchArgs &A, const vor_opts *o, void *ws, const L
     PM.need_out = nullptr;
     PM.need_in = nullptr;
     PM.store_poly = 0;
+    PM.seed_poly = L.lanes == 1 ? 1 : 0;     // the thread passes left their polygons
     PM.cell_list = med_list;
     PM.list_count = med_count;
     PM.n_list = n;
