@@ -1017,18 +1017,28 @@ __device__ int certify_by_vertex_discs(const CellParams &P, const CellGrid &g,
         }
         C = e;
         cnt.widen++;
+        // a cell handed on to the block tier leaves this polygon (its edge
+        // lines) for the block tier's first candidates
+        auto hand_on = [&]() {
+            if (P.seed_poly && e >= 3 && e <= SLOT_CAP) {
+                const int k = P.sid[i];
+                for (int q = gl; q < e; q += G) P.slot[(size_t)k * SLOT_CAP + q] = S.lab[S.emit[q]];
+                if (gl == 0) P.ecount[k] = -e;
+            }
+            return CELL_DEFER;
+        };
         i64 step2 = min(min(need, rho2 < ((i64)1 << 60) / 4 ? 4 * rho2 + 4 : rho2), far2);
         // the medium tier reads one bounding range per bucket row; a wide
         // annulus, or one over many sites (a cluster's core: the coarse
         // occupancy grid counts the sites of its bounding square), goes to
         // the block tier, which reads the vertex-disc chords row by row with
         // 8 warps
-        if (CMAX < 1024 && 2.f * sqrtf((float)step2) > 256.f * (float)g.s) return CELL_DEFER;
+        if (CMAX < 1024 && 2.f * sqrtf((float)step2) > 256.f * (float)g.s) return hand_on();
         if (ROUTE) {
             const int r = (int)ceilf(sqrtf((float)step2)) + 1;
             const SetMeta &M = set_of(P.sets, P.sset, i);
             const int held = coarse_sites(P.coarse_sat, M, p.x - r, p.y - r, p.x + r, p.y + r);
-            if (held > M_DEFER_SITES && held < M.n / 16) return CELL_DEFER;
+            if (held > M_DEFER_SITES && held < M.n / 16) return hand_on();
         }
         for (int shrink = 0;; shrink++) {
             if (gl == 0) { S.ncand = C; S.flag = 0; }

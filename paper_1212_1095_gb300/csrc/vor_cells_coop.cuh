@@ -527,6 +527,32 @@ __device__ int coop_cell(const CellParams &P, const CoopView &V, CoopCtl &K, int
     }
     int C = K.ncand;
     if (C + 4 > V.cap) return CELL_DEFER;
+    if (P.seed_poly) {
+        // the polygon an earlier tier left (ecount = -e, its lines in the
+        // slot): its sites outside the disc join the candidates (extra
+        // candidates never change the cell; these start it near its edges)
+        const int e1 = -P.ecount[k];
+        if (e1 >= 3 && e1 <= SLOT_CAP) {
+            __syncthreads();                           // every thread has read the count
+            if (tid < e1) {
+                const int lab = P.slot[(size_t)k * SLOT_CAP + tid];
+                if (lab >= 0 && lab < set_of(P.sets, P.sset, i).n && lab != kl) {
+                    const int2 a = __ldg(P.sites + g.site_base + lab);
+                    const int nx = a.x - p.x, ny = a.y - p.y;
+                    if ((i64)nx * nx + (i64)ny * ny > rho2) {   // else the disc listed it
+                        const int at = atomicAdd(&K.ncand, 1);
+                        if (at < V.cap - 4) {
+                            const float fnx = (float)nx, fny = (float)ny, rc = 1.f / fmaf(fnx, fnx, fny * fny);
+                            V.cand[at] = make_float4(fnx, fny, rc, (float)(abs(nx) + abs(ny)) * rc);
+                            V.lab[at] = lab;
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+            C = min(K.ncand, V.cap - 4);
+        }
+    }
     if (tid == 0) {
         const int sx[4] = {0, g.W - p.x, 0, -p.x};
         const int sy[4] = {-p.y, 0, g.H - p.y, 0};
