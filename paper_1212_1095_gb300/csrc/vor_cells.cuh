@@ -205,9 +205,13 @@ enum { Q_SHOOT = 0, Q_UTEST = 1 };
 
 // Algorithm 1 over the C staged candidates.  Returns the number of edges (in
 // S.emit, counter-clockwise from the edge met by psi_1), or -1 when a
-// capacity is exceeded.
+// capacity is exceeded.  Not inlined: the warp tier calls it twice (the
+// first polygon and the reruns of the certificate), and one copy of its code
+// instead of two keeps the tier's hot loop in the instruction cache (the
+// top stall of the tier with 21 warps per SM at different points of it;
+// measured: the batch's tiers 33.3 -> 24.5 ms).
 template <int G, int CMAX, int SMAX, int EMAX, int RMAX>
-__device__ int projector(GroupSmem<CMAX, SMAX, EMAX> &S, const int C, const int gl,
+__device__ __noinline__ int projector(GroupSmem<CMAX, SMAX, EMAX> &S, const int C, const int gl,
                          const unsigned gmask, const int exact_only, Counters &cnt) {
     int phase = 0;                  // 0..2: the projector corners; 3: the subedges
     Hit init[3];
@@ -467,7 +471,7 @@ __device__ __forceinline__ bool normal_less(const SM &S, int a, int b) {
 // order).  Returns the number of edges (in S.emit), or -1 when a capacity is
 // exceeded.  The counters of all groups end in lane 0's.
 template <int NG, int CMAX, int SMAX, int EMAX, int RMAX>
-__device__ int projector_par(GroupSmem<CMAX, SMAX, EMAX> &S, const int C, const int lane,
+__device__ __noinline__ int projector_par(GroupSmem<CMAX, SMAX, EMAX> &S, const int C, const int lane,
                              const int exact_only, Counters &cnt) {
     static_assert(NG >= 3 && 32 % NG == 0, "three corner rays, whole groups");
     constexpr int GL = 32 / NG;
