@@ -242,42 +242,50 @@ __global__ void __launch_bounds__(32 * FL_WARPS) flower_gather_kernel(CellParams
             }
             r2max = fminf(r2max, (float)lim2);
         }
-        // pass 1: the flower's sites by distance from p (32 bins of |a - p|^2)
+        // two walks over the same rows with one copy of the walk's code: the
+        // first counts the flower's sites by distance from p (32 bins of
+        // |a - p|^2), the second lists those that fit (entry order does not
+        // change the cell)
         const float binscale = 32.f / fmaxf(r2max, 1.f);
-        auto count = [&](int pos, int2 q) {
+        bool listing = false;
+        i64 rho2 = 0;
+        auto visit = [&](int pos, int2 q) {
             if (pos == i) return;
             const int ax = q.x - p.x, ay = q.y - p.y;
             const i64 dd = (i64)ax * ax + (i64)ay * ay;
             if (dd >= lim2 || !in_flower(F, F.disc[q.y / s - rb0], ax, ay)) return;
-            atomicAdd(&F.hist[min(31, (int)((float)dd * binscale))], 1);
-        };
-        scan_rows<32, 1, 2>(g, P.sxy, by0, by1, lane, FULL, span, count);
-        __syncwarp();
-        // the nearest bins that fit: all of them (a complete list), or those
-        // below bin b (every flower site with |a - p|^2 < b r2max / 32)
-        int b = 0, sum = 0;
-        while (b < 32 && sum + F.hist[b] <= GMAX) sum += F.hist[b++];
-        if (b < 32) lim2 = min(lim2, (i64)((float)b / binscale));   // the bins below b
-        // certificate radius: unbounded when the whole flower is listed, else
-        // every flower site with |a - p|^2 <= rho2 is listed
-        const i64 rho2 = lim2 == LLONG_MAX ? LLONG_MAX : lim2 - 1;
-        if (rho2 < 1) {
-            if (lane == 0) { G.count[t] = -1; G.rho2[t] = 0; }
-            continue;
-        }
-        // pass 2: list them (entry order does not change the cell)
-        auto list = [&](int pos, int2 q) {
-            if (pos == i) return;
-            const int ax = q.x - p.x, ay = q.y - p.y;
-            if ((i64)ax * ax + (i64)ay * ay >= lim2 || !in_flower(F, F.disc[q.y / s - rb0], ax, ay)) return;
+            if (!listing) {
+                atomicAdd(&F.hist[min(31, (int)((float)dd * binscale))], 1);
+                return;
+            }
             const int at = atomicAdd(&F.cnt, 1);
             if (at < GMAX) {
                 G.tab[G.at(t, at)] = t1::cand_of(ax, ay);
                 G.lab[G.at(t, at)] = __ldg(P.sid + pos) - g.site_base;
             }
         };
-        scan_rows<32, 1, 2>(g, P.sxy, by0, by1, lane, FULL, span, list);
-        __syncwarp();
+        bool done = false;
+#pragma unroll 1
+        for (int walk = 0; walk < 2; walk++) {
+            scan_rows<32, 1, 2>(g, P.sxy, by0, by1, lane, FULL, span, visit);
+            __syncwarp();
+            if (walk == 1) break;
+            // the nearest bins that fit: all of them (a complete list), or
+            // those below bin b (every flower site with |a - p|^2 < b r2max / 32)
+            int b = 0, sum = 0;
+            while (b < 32 && sum + F.hist[b] <= GMAX) sum += F.hist[b++];
+            if (b < 32) lim2 = min(lim2, (i64)((float)b / binscale));   // the bins below b
+            // certificate radius: unbounded when the whole flower is listed,
+            // else every flower site with |a - p|^2 <= rho2 is listed
+            rho2 = lim2 == LLONG_MAX ? LLONG_MAX : lim2 - 1;
+            if (rho2 < 1) {
+                if (lane == 0) { G.count[t] = -1; G.rho2[t] = 0; }
+                done = true;
+                break;
+            }
+            listing = true;
+        }
+        if (done) continue;
         if (lane == 0) {
             const int n_list = F.cnt;
             G.count[t] = n_list <= GMAX ? n_list : -1;
