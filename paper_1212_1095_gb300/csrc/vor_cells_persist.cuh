@@ -29,7 +29,7 @@ constexpr int P_NT = 64, P_SMAX = 16, P_EMAX = 16, P_RMAX = 32;
 constexpr int P_REFILL = 32;         // idle lanes that trigger a batched refill (all)
 // first pass: 4 sides + up to 40 sites; second pass (the cells the first
 // disc did not certify): a disc with about 2.2 times the sites, 4 + 72
-// entries; third pass: the flower of the polygon an earlier pass left
+// entries; flower passes: the flower of the polygon an earlier pass left
 // (vor_flower.cuh), 4 + 124 entries
 constexpr int P1_CMAX = 44, P2_CMAX = 76, P3_CMAX = 128;
 

@@ -1,4 +1,4 @@
-// vor_flower.cuh -- the flower gather of the third thread-per-cell pass:
+// vor_flower.cuh -- the flower gather of the thread-per-cell flower passes:
 // one warp lists the candidates of one cell from the polygon an earlier pass
 // left in the cell's slot.
 //
