@@ -29,7 +29,7 @@ enum {
 // (batches).  Measured on the 4,096-set batch: three passes leave 252 k cells
 // to the warp tier, two leave 284 k, but the third pass costs more than the
 // warp tier spends on the difference (batch 110.1 ms with three, 108.8 ms
-// with two).
+// with two, 111.8 ms with one).
 constexpr int FLOWER_PASSES = 2;
 
 // Workspace header (first 256 bytes of the workspace).
