@@ -796,6 +796,10 @@ __global__ void __launch_bounds__(NT) cells_persist_kernel(CellParams P, GatherO
         float u1b = -FLT_MAX, u2b = -FLT_MAX, lsb = -FLT_MAX;
         int i1a = -1, i1b = -1;
         int c = 4;
+        // unrolled twice: the next pair's loads and keys overlap this pair's
+        // comparisons (measured: 0.857 -> 0.842 ms; four streams instead of
+        // two cost registers and ran at 1.04 ms)
+#pragma unroll 2
         for (; c + 1 < Cq; c += 2) {
             float Ua, La, Ub, Lb;
             t1::filter_keys(T.get(c), false, fx, fy, eth, Ua, La);
