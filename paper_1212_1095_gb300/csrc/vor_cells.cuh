@@ -282,6 +282,9 @@ __device__ __noinline__ int projector(GroupSmem<CMAX, SMAX, EMAX> &S, const int 
         const float fx = (float)tx, fy = (float)ty;
         const float eth = fmaxf(fabsf(fx), fabsf(fy)) * VOR_TOL_SCALE;
         Filt f{-FLT_MAX, -FLT_MAX, -FLT_MAX, -FLT_MAX, -1};
+        // unrolled twice: a lane's next candidate loads while this one is
+        // compared (measured: the batch's tiers 26.5 -> 23.4 ms)
+#pragma unroll 2
         for (int c = gl; c < C; c += G) {
             const float4 q = S.cand[c];
             const float den = fmaf(q.x, fx, q.y * fy);
@@ -392,6 +395,7 @@ __device__ bool group_shoot(const SM &S, int C, int qt, i64 tx, i64 ty, int la, 
     const float fx = (float)tx, fy = (float)ty;
     const float eth = fmaxf(fabsf(fx), fabsf(fy)) * VOR_TOL_SCALE;
     Filt f{-FLT_MAX, -FLT_MAX, -FLT_MAX, -FLT_MAX, -1};
+#pragma unroll 2
     for (int c = gl; c < C; c += GL) {
         const float4 q = S.cand[c];
         const float den = fmaf(q.x, fx, q.y * fy);
