@@ -38,8 +38,10 @@
 // cells the thread-per-cell passes leave, certifies them with the vertex
 // discs of the polygon (flower) over growing annuli, and hands the cells
 // that exceed it, or whose next annulus lies over a cluster's core, to the
-// block tier (vor_cells_coop.cuh).  For a single diagram the warp tier runs
-// a cell's subedges on four groups of 8 lanes (projector_par).
+// block tier (vor_cells_coop.cuh).  Its first candidates include the sites
+// of the polygon the last pass left in the cell's slot, and it leaves its
+// own polygon there for the block tier.  For a single diagram the warp tier
+// runs a cell's subedges on four groups of 8 lanes (projector_par).
 #pragma once
 
 #include <cfloat>
