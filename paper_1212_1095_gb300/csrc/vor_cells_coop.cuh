@@ -20,8 +20,9 @@
 // order.  Consecutive edges meet at the vertices.
 //
 // Candidates and certificate are those of the warp-per-cell tiers: the sites
-// within rho of p, then the vertex-disc ("flower") certificate, whose bucket
-// rows are now spread over all warps of the block.
+// within rho of p (with the sites of the polygon the warp tier handed on),
+// then the vertex-disc ("flower") certificate, whose bucket rows are now
+// spread over all warps of the block.
 //
 // Two modes share the code.  Mode S keeps a cell's arrays in shared memory
 // with fixed capacities; a cell that exceeds them is handed to mode G, which
